@@ -22,7 +22,8 @@ Readings:
 * The gradient is the exact derivative of this truncated forward pass with the
   kept count k held fixed (the "local" approach of Sec. 4 made exact): the SVD is
   differentiated through M = C~^+ C~ = V diag(s^2) V^+ with the full spectrum,
-  F_ij = (w_j - w_i) / ((w_j - w_i)^2 + eta), eta = (1e-12 w_1)^2.
+  F_ij = (w_j - w_i) / ((w_j - w_i)^2 + eta), eta = (1e-12 w_1)^2; singular values at
+  or below 1e-13 s_1 count as exact zeros there (see NULL_REL).
 """
 from __future__ import annotations
 
@@ -34,6 +35,10 @@ import numpy as np
 from . import pauli
 
 ETA_REL = 1e-12
+# Singular values at or below NULL_REL * s_1 are rounding noise of an exactly rank-deficient
+# matrix (particle-number and spin symmetry make many two-site tensors rank deficient); the
+# adjoint treats them as exact zeros: w_i = 0 and the column (C~ V)_i = 0.
+NULL_REL = 1e-13
 
 
 @dataclass
@@ -217,11 +222,15 @@ def svd_adjoint(Cm, s, V, k, sbar_k, Vbar_k):
     M = C~^+ C~ = V diag(w) V^+, w = s^2 padded with zeros to the column count.
     dE = sum wbar dw + 2 Re <Vbar, dV> gives, with J = F o (V^+ Vbar),
     Mbar = V (diag(wbar) + J + J^+) V^+ (Hermitian, dE = tr(Mbar dM)) and
-    C~bar = C~ Mbar.
+    C~bar = C~ Mbar = (C~ V)(diag(wbar) + J + J^+) V^+, where the columns of C~ V that
+    belong to numerical zeros (s_i <= NULL_REL s_1) are set to zero.
     """
     ncol = V.shape[0]
     w = np.zeros(ncol)
     w[: len(s)] = s * s
+    null = np.ones(ncol, dtype=bool)
+    null[: len(s)] = s <= NULL_REL * s[0]
+    w[null] = 0.0
     wbar = np.zeros(ncol)
     wbar[:k] = sbar_k / (2.0 * s[:k])
     Vbar = np.zeros((ncol, ncol), dtype=complex)
@@ -231,8 +240,9 @@ def svd_adjoint(Cm, s, V, k, sbar_k, Vbar_k):
     F = dw / (dw * dw + eta)
     np.fill_diagonal(F, 0.0)
     J = F * (V.conj().T @ Vbar)
-    Mbar = V @ (np.diag(wbar) + J + J.conj().T) @ V.conj().T
-    return Cm @ Mbar
+    W = Cm @ V
+    W[:, null] = 0.0
+    return W @ (np.diag(wbar) + J + J.conj().T) @ V.conj().T
 
 
 def gate_adjoint(tape, Bbar_l_new, Bbar_r_new, lambar_new, dG):
