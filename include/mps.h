@@ -1,0 +1,201 @@
+/*
+ * libmps: GB300-native (sm_103a) differentiable matrix-product-state simulator
+ * for variational quantum chemistry circuits (arXiv:2211.07983).
+ *
+ * C ABI: plain pointers and sizes, no C++ types, no exceptions.  Every entry
+ * point returns an mps_status; on error the outputs are left untouched and
+ * mps_last_error() returns a thread-local message.  Nothing aborts, traps or
+ * asserts on the device: device-side failures are reported through a status
+ * word that the host reads after the call's stream work completes.
+ *
+ * Memory: the library allocates and owns the device memory of every handle it
+ * returns (mps_state, mps_circuit, mps_hamiltonian_dev) until the matching
+ * *_free call.  Inputs are copied; the caller keeps ownership of its arrays.
+ * Arrays marked "host or device" may point to host memory or to device memory
+ * of the current CUDA device (the library asks the driver which it is).
+ *
+ * Streams: all device work of a call is ordered on mps_config.cuda_stream
+ * (NULL = the legacy default stream).  Every call that launches device work
+ * synchronises that stream before returning, because it reads the device status
+ * word; outputs may still be device pointers (no host round trip of the data).
+ *
+ * Notation (Sec. 3): n qubits = n sites; site tensor B_s[Dl][2][Dr], row-major,
+ * Dr fastest; bond b joins sites b and b+1 and carries the Schmidt vector
+ * lambda_b; bond dimensions never exceed min(2^(b+1), 2^(n-b-1), max_bond).
+ */
+#ifndef MPS_H
+#define MPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MPS_OK = 0,
+  MPS_EINVAL = 1,    /* invalid argument (sizes, indices, non-finite angle) */
+  MPS_ENOMEM = 2,    /* device or host allocation failed */
+  MPS_ECUDA = 3,     /* a CUDA runtime call failed */
+  MPS_ENOCONV = 4,   /* one-sided Jacobi SVD did not converge within its sweep cap */
+  MPS_ENUMERIC = 5,  /* NaN/Inf met in a singular value, a norm or the energy */
+  MPS_ETIMEOUT = 6   /* a bounded device wait gave up */
+} mps_status;
+
+enum { MPS_PRECISION_FP64 = 0, MPS_PRECISION_MIXED = 1 };
+
+/* Simulation settings (Sec. 3 truncation rule; Sec. 4 checkpointed reverse pass). */
+typedef struct {
+  int32_t max_bond;          /* D: bond-dimension cap, >= 1 */
+  double cutoff;             /* eps: keep singular values with s_i/||s||_2 > eps */
+  int32_t precision;         /* MPS_PRECISION_FP64 (only value accepted by this build) */
+  int32_t checkpoint_every;  /* reverse pass: MPS snapshot every k gates; 0 = 512 */
+  void* cuda_stream;         /* cudaStream_t, NULL = default stream */
+} mps_config;
+
+/*
+ * One fused nearest-neighbour gate on sites (bond, bond+1) (Sec. 3, two-qubit
+ * gate; gate fusion).  Matrices are 4x4 complex, row-major, interleaved
+ * (re, im), basis index 2*i_bond + i_{bond+1}.
+ *   theta_idx < 0 : G = mat (pre/post ignored)
+ *   theta_idx >= 0: G(phi) = post * Rz_site(phi) * pre, phi = theta_scale *
+ *                   theta[theta_idx], Rz(phi) = diag(e^{-i phi/2}, e^{i phi/2})
+ *                   on the lower (rz_site = 0) or upper (rz_site = 1) site.
+ */
+typedef struct {
+  int32_t bond;
+  int32_t theta_idx;
+  int32_t rz_site;
+  int32_t pad_;
+  double theta_scale;
+  double mat[32];
+  double pre[32];
+  double post[32];
+} mps_gate;
+
+/*
+ * Weighted Pauli strings H = sum_k coeff[k] P_k (Sec. 2, Eq. expect-val).
+ * Bit s of x_mask/z_mask is qubit s: (x,z) = (1,0) X, (0,1) Z, (1,1) Y.
+ * Host arrays; any order (the library sorts them canonically).
+ */
+typedef struct {
+  int32_t n_terms;
+  const uint64_t* x_mask;
+  const uint64_t* z_mask;
+  const double* coeff;
+} mps_hamiltonian;
+
+typedef struct mps_state mps_state;              /* MPS on the device */
+typedef struct mps_circuit mps_circuit;          /* gate list resident on the device */
+typedef struct mps_hamiltonian_dev mps_hamiltonian_dev; /* strings + sweep trie on the device */
+
+/* ---- host-side problem builders (step S0: once per problem) ----------------------- */
+
+/*
+ * Jordan-Wigner qubit Hamiltonian of H = sum h_pq a+_p a_q
+ * + 1/2 sum (pq|rs) a+_p a+_r a_s a_q (Sec. 2, Eq. ham-pbc, chemist notation),
+ * with a_p = Z_0..Z_{p-1} (X_p + iY_p)/2.  Contributions to one string are merged
+ * by their correctly rounded exact sum; strings with |c| <= 1e-14 max|c| are
+ * dropped; output in canonical order (first non-identity site, then the
+ * per-site symbols I<X<Y<Z; the identity first).
+ *   n      : spin orbitals, 1..64
+ *   h      : host, n*n doubles, h[p*n+q]
+ *   eri    : host, n^4 doubles, eri[((p*n+q)*n+r)*n+s] = (pq|rs)
+ *   capacity, x_mask, z_mask, coeff: host output arrays of `capacity` entries
+ *   n_terms_out: number of strings.  If it exceeds capacity, nothing is written
+ *           to the arrays and MPS_EINVAL is returned (call again with room).
+ */
+mps_status mps_build_hamiltonian(int32_t n, const double* h, const double* eri, int64_t capacity,
+                                 uint64_t* x_mask, uint64_t* z_mask, double* coeff,
+                                 int64_t* n_terms_out);
+
+/*
+ * UCC excitations -> fused nearest-neighbour gates (Sec. 2, UCC ansatz with a
+ * first-order Trotter step of "V-shaped" blocks; Sec. 3, gate fusion).
+ *   exc: host, 4*n_exc ints (i, j, a, b); a single i->a has j = b = -1 and
+ *        generator a+_a a_i - h.c.; a double has a+_a a+_b a_j a_i - h.c.
+ *        Excitation t uses angle theta[t]; excitations are applied in order.
+ *   gates_out: host array of `capacity` gates; n_gates_out: count.  Too small a
+ *        capacity writes nothing and returns MPS_EINVAL with the count set.
+ */
+mps_status mps_compile_excitations(int32_t n, const int32_t* exc, int32_t n_exc, int64_t capacity,
+                                   mps_gate* gates_out, int64_t* n_gates_out);
+
+/* ---- simulator (steps S1-S9) --------------------------------------------------------- */
+
+/* Product state |b_0 ... b_{n-1}> as a D = 1 MPS with all lambda = [1] (Sec. 3, Eq. hf).
+ * bits: host, n bytes of 0/1.  n in 2..64. */
+mps_status mps_init_product(int32_t n_qubits, const uint8_t* bits, const mps_config* cfg,
+                            mps_state** out);
+
+/* Deep copy of a state (same config and stream). */
+mps_status mps_clone(const mps_state* s, mps_state** out);
+
+/* Copy a state back to the host.  dims: n+1 ints (bond dims, dims[0] = dims[n] = 1);
+ * lam: sum of dims[1..n-1] doubles (lambda_0, lambda_1, ...), or NULL;
+ * tensors: sum_s dims[s]*2*dims[s+1] complex values as interleaved doubles,
+ * sites in order, each [Dl][2][Dr] row-major, or NULL. */
+mps_status mps_read_state(const mps_state* s, int32_t* dims, double* lam, double* tensors);
+
+/* Upload a gate list once (validated: bonds in range, finite matrices). */
+mps_status mps_circuit_create(int32_t n_qubits, const mps_gate* gates, int32_t n_gates,
+                              mps_circuit** out);
+void mps_circuit_free(mps_circuit* c);
+
+/* Upload a Hamiltonian once; builds the sweep trie (strings sharing a first site
+ * form a batch; strings sharing a prefix share its environments). */
+mps_status mps_hamiltonian_create(int32_t n_qubits, const mps_hamiltonian* h,
+                                  mps_hamiltonian_dev** out);
+void mps_hamiltonian_free(mps_hamiltonian_dev* h);
+
+/*
+ * In place |s> <- U(theta)|s> (Sec. 3: each gate = two-site contraction, lambda
+ * scaling, SVD, truncation, update; Sec. 4, Eq. pqc).  theta: host or device,
+ * n_theta doubles, finite; every theta_idx must be < n_theta.
+ */
+mps_status mps_apply_circuit(mps_state* s, const mps_gate* gates, int32_t n_gates,
+                             const double* theta, int32_t n_theta);
+mps_status mps_apply_circuit_dev(mps_state* s, const mps_circuit* c, const double* theta,
+                                 int32_t n_theta);
+
+/*
+ * E = sum_k c_k Re<psi|P_k|psi> / <psi|psi> (Sec. 2, Eq. expect-val; Sec. 3, Eq.
+ * paulistringexp) by batched transfer-matrix sweeps.  E_out: host or device double.
+ * expect_out: NULL, or host/device array with one double per non-identity string,
+ * receiving Re<psi|P_k|psi>/<psi|psi> in canonical order (first non-identity site,
+ * then the per-site symbols I<X<Y<Z).
+ */
+mps_status mps_energy(const mps_state* s, const mps_hamiltonian* h, double* E_out);
+mps_status mps_energy_dev(const mps_state* s, const mps_hamiltonian_dev* h, double* E_out,
+                          double* expect_out);
+
+/*
+ * E(theta) and dE/dtheta for |psi> = U(theta)|s0> (s0 is not modified): forward
+ * pass with snapshots, energy, energy cotangent dE/dB* (Sec. 4, Eq. expecgrad),
+ * then the exact reverse pass through every truncated gate (Eq. circuitevolvegrad,
+ * App. A rules), k held fixed.  grad_out: n_theta doubles; gate_grad_out: NULL or
+ * n_gates doubles receiving dE/dphi of each gate's Rz angle (0 for fixed gates).
+ * All three outputs: host or device.
+ */
+mps_status mps_energy_grad(const mps_state* s0, const mps_gate* gates, int32_t n_gates,
+                           const double* theta, int32_t n_theta, const mps_hamiltonian* h,
+                           double* E_out, double* grad_out, double* gate_grad_out);
+mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const double* theta,
+                               int32_t n_theta, const mps_hamiltonian_dev* h, double* E_out,
+                               double* grad_out, double* gate_grad_out);
+
+/* Release a state (NULL-safe). */
+void mps_free(mps_state* s);
+
+/* Thread-local text of the last error of this thread ("" if none). */
+const char* mps_last_error(void);
+
+/* Kernel launches issued by this process so far (instrumentation for benchmarks). */
+int64_t mps_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPS_H */

@@ -1,0 +1,229 @@
+"""Python face of libmps: the same calls as include/mps.h, with numpy / torch arrays.
+
+Every step of the computation runs in libmps; this module only turns Python objects
+into pointers and sizes.  Array arguments may be numpy arrays (host) or torch tensors
+(host or CUDA); CUDA tensors are passed as device pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import GATE_DTYPE, MpsConfig, MpsHamiltonian, check
+
+P = ctypes.POINTER
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _f64(a):
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64:
+            raise TypeError("float64 tensor expected")
+        return a
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream      # torch.cuda.Stream
+
+
+# ---- step S0: host builders ---------------------------------------------------------------
+
+def build_hamiltonian(h: np.ndarray, eri: np.ndarray):
+    """mps_build_hamiltonian: integrals -> (x_mask, z_mask, coeff) in canonical order."""
+    lib = _lib.load()
+    n = int(h.shape[0])
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    cnt = ctypes.c_int64(0)
+    code = lib.mps_build_hamiltonian(n, h.ctypes.data_as(P(ctypes.c_double)),
+                                     eri.ctypes.data_as(P(ctypes.c_double)), 0, None, None, None,
+                                     ctypes.byref(cnt))
+    if code != 1 or cnt.value <= 0:
+        check(code)
+    m = cnt.value
+    x = np.zeros(m, dtype=np.uint64)
+    z = np.zeros(m, dtype=np.uint64)
+    c = np.zeros(m, dtype=np.float64)
+    check(lib.mps_build_hamiltonian(n, h.ctypes.data_as(P(ctypes.c_double)), eri.ctypes.data_as(P(ctypes.c_double)),
+                                    m, x.ctypes.data_as(P(ctypes.c_uint64)), z.ctypes.data_as(P(ctypes.c_uint64)),
+                                    c.ctypes.data_as(P(ctypes.c_double)), ctypes.byref(cnt)))
+    return x, z, c
+
+
+def compile_excitations(n: int, excitations) -> np.ndarray:
+    """mps_compile_excitations: [(i, j, a, b)] -> structured array of mps_gate (GATE_DTYPE)."""
+    lib = _lib.load()
+    exc = np.ascontiguousarray(np.asarray(excitations, dtype=np.int32).reshape(-1, 4))
+    cnt = ctypes.c_int64(0)
+    code = lib.mps_compile_excitations(n, exc.ctypes.data_as(P(ctypes.c_int32)), len(exc), 0, None,
+                                       ctypes.byref(cnt))
+    if code != 1 or cnt.value < 0:
+        check(code)
+    gates = np.zeros(cnt.value, dtype=GATE_DTYPE)
+    check(lib.mps_compile_excitations(n, exc.ctypes.data_as(P(ctypes.c_int32)), len(exc), cnt.value,
+                                      ctypes.c_void_p(gates.ctypes.data), ctypes.byref(cnt)))
+    return gates
+
+
+# ---- handles --------------------------------------------------------------------------------
+
+class State:
+    """mps_state: an MPS resident on the GPU (mps_init_product / mps_clone / mps_free)."""
+
+    def __init__(self, handle, n):
+        self._h = handle
+        self.n = n
+
+    @classmethod
+    def product(cls, bits, max_bond: int, cutoff: float, checkpoint_every: int = 0, stream=None):
+        lib = _lib.load()
+        bits = np.ascontiguousarray(bits, dtype=np.uint8)
+        cfg = MpsConfig(max_bond, cutoff, _lib.PRECISION_FP64, checkpoint_every, _stream_handle(stream))
+        h = ctypes.c_void_p()
+        check(lib.mps_init_product(len(bits), bits.ctypes.data_as(P(ctypes.c_uint8)), ctypes.byref(cfg),
+                                   ctypes.byref(h)))
+        return cls(h, len(bits))
+
+    def clone(self):
+        h = ctypes.c_void_p()
+        check(_lib.load().mps_clone(self._h, ctypes.byref(h)))
+        return State(h, self.n)
+
+    def read(self):
+        """(dims, lambdas per bond, site tensors) copied to the host."""
+        lib = _lib.load()
+        dims = np.zeros(self.n + 1, dtype=np.int32)
+        check(lib.mps_read_state(self._h, dims.ctypes.data_as(P(ctypes.c_int32)), None, None))
+        nl = int(dims[1:-1].sum())
+        ne = int(sum(dims[s] * 2 * dims[s + 1] for s in range(self.n)))
+        lam = np.zeros(max(nl, 1))
+        ten = np.zeros(2 * max(ne, 1))
+        check(lib.mps_read_state(self._h, dims.ctypes.data_as(P(ctypes.c_int32)),
+                                 lam.ctypes.data_as(P(ctypes.c_double)), ten.ctypes.data_as(P(ctypes.c_double))))
+        lams, o = [], 0
+        for b in range(1, self.n):
+            lams.append(lam[o:o + dims[b]].copy())
+            o += dims[b]
+        cplx = ten[: 2 * ne].view(np.complex128)
+        B, o = [], 0
+        for s in range(self.n):
+            e = dims[s] * 2 * dims[s + 1]
+            B.append(cplx[o:o + e].reshape(dims[s], 2, dims[s + 1]).copy())
+            o += e
+        return dims, lams, B
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            _lib.load().mps_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Circuit:
+    """mps_circuit: a gate list uploaded once."""
+
+    def __init__(self, n: int, gates: np.ndarray):
+        gates = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+        self.n, self.n_gates = n, len(gates)
+        self.n_theta = int(gates["theta_idx"].max()) + 1 if len(gates) else 0
+        h = ctypes.c_void_p()
+        check(_lib.load().mps_circuit_create(n, ctypes.c_void_p(gates.ctypes.data), len(gates), ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        try:
+            if self._h is not None and self._h.value:
+                _lib.load().mps_circuit_free(self._h)
+        except Exception:
+            pass
+
+
+def _ham_struct(x, z, c):
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    z = np.ascontiguousarray(z, dtype=np.uint64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    hs = MpsHamiltonian(len(c), x.ctypes.data_as(P(ctypes.c_uint64)), z.ctypes.data_as(P(ctypes.c_uint64)),
+                        c.ctypes.data_as(P(ctypes.c_double)))
+    return hs, (x, z, c)
+
+
+class Hamiltonian:
+    """mps_hamiltonian_dev: Pauli strings + sweep trie uploaded once."""
+
+    def __init__(self, n: int, x, z, c):
+        hs, keep = _ham_struct(x, z, c)
+        h = ctypes.c_void_p()
+        check(_lib.load().mps_hamiltonian_create(n, ctypes.byref(hs), ctypes.byref(h)))
+        self._h, self.n = h, n
+        # expectations are reported for the non-identity strings only
+        self.n_terms = int(np.count_nonzero((keep[0] | keep[1]) != 0))
+
+    def __del__(self):
+        try:
+            if self._h is not None and self._h.value:
+                _lib.load().mps_hamiltonian_free(self._h)
+        except Exception:
+            pass
+
+
+# ---- steps S1-S9 ----------------------------------------------------------------------------
+
+def apply_circuit(state: State, circuit: Circuit, theta) -> None:
+    """mps_apply_circuit_dev: |state> <- U(theta)|state>."""
+    theta = _f64(theta)
+    check(_lib.load().mps_apply_circuit_dev(state._h, circuit._h, _ptr(theta), len(theta)))
+
+
+def energy(state: State, ham: Hamiltonian, expect=False):
+    """mps_energy_dev: E (and optionally Re<P_k>/<psi|psi> in canonical order)."""
+    E = np.zeros(1)
+    ex = np.zeros(ham.n_terms) if expect else None
+    check(_lib.load().mps_energy_dev(state._h, ham._h, _ptr(E), _ptr(ex)))
+    return (float(E[0]), ex) if expect else float(E[0])
+
+
+def energy_grad(state0: State, circuit: Circuit, theta, ham: Hamiltonian, out=None, gate_grad=False):
+    """mps_energy_grad_dev: E(theta), dE/dtheta (and dE/dphi per gate) of U(theta)|state0>.
+
+    `out`: optional (E, grad) arrays/tensors receiving the results (may be CUDA tensors).
+    """
+    theta = _f64(theta)
+    if out is None:
+        E_out, g_out = np.zeros(1), np.zeros(len(theta))
+    else:
+        E_out, g_out = out
+    gg = np.zeros(circuit.n_gates) if gate_grad else None
+    check(_lib.load().mps_energy_grad_dev(state0._h, circuit._h, _ptr(theta), len(theta), ham._h, _ptr(E_out),
+                                          _ptr(g_out), _ptr(gg)))
+    if out is not None:
+        return out
+    return (float(E_out[0]), g_out, gg) if gate_grad else (float(E_out[0]), g_out)
+
+
+def kernel_launches() -> int:
+    return int(_lib.load().mps_kernel_launches())

@@ -1,0 +1,111 @@
+// Batched complex FP64 GEMM driven by device-resident descriptors (see GemmDesc).
+//
+// Every bond contraction of the FP64 path (the site update B~_n = C V_k, the transfer
+// matrices of the Pauli sweeps, the environment contractions of the energy cotangent and
+// the GEMMs of the gate adjoints) is expressed as one or more descriptors; one launch
+// executes a batch of independent descriptors.  Tiles that fall outside a descriptor's
+// run-time M x N exit at once, so a launch can be sized for the bond-dimension caps.
+//
+// Tile: 64 x 64 outputs per 256-thread CTA, 4 x 4 per thread, K staged through shared
+// memory in chunks of 8.  FP64 on GB300 runs at a small fraction of the FP32 rate, so this
+// SIMT kernel is bound by the FP64 pipe, not by memory, once a tile is resident.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace mpsk {
+
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 8;
+
+__device__ __forceinline__ double2 load_op(const double2* X, int ld, int op, int r, int c) {
+  // element (r, c) of op(X)
+  switch (op) {
+    case OP_N: return X[(size_t)r * ld + c];
+    case OP_T: return X[(size_t)c * ld + r];
+    case OP_H: return conjd(X[(size_t)c * ld + r]);
+    default: return conjd(X[(size_t)r * ld + c]);
+  }
+}
+
+__device__ __forceinline__ void gemm_tile(const GemmDesc& d) {
+  const int M = deval(d.M, d.dims), N = deval(d.N, d.dims), K = deval(d.K, d.dims);
+  const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TN;
+  if (row0 >= M || col0 >= N || M <= 0 || N <= 0) return;
+  const int lda = deval(d.lda, d.dims), ldb = deval(d.ldb, d.dims), ldc = deval(d.ldc, d.dims);
+  __shared__ double2 As[TK][TM + 1];
+  __shared__ double2 Bs[TK][TN + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < K; k0 += TK) {
+    for (int e = threadIdx.x; e < TK * TM; e += 256) {
+      int kk = e / TM, ii = e % TM;
+      int r = row0 + ii, c = k0 + kk;
+      As[kk][ii] = (r < M && c < K) ? load_op(d.A, lda, d.opA, r, c) : make_double2(0.0, 0.0);
+    }
+    for (int e = threadIdx.x; e < TK * TN; e += 256) {
+      int kk = e / TN, jj = e % TN;
+      int r = k0 + kk, c = col0 + jj;
+      Bs[kk][jj] = (r < K && c < N) ? load_op(d.B, ldb, d.opB, r, c) : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      double2 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = cfma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  const bool zero_beta = (d.beta.x == 0.0 && d.beta.y == 0.0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int r = row0 + ty + 16 * i;
+    if (r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int c = col0 + tx + 16 * j;
+      if (c >= N) continue;
+      double2 v = cmul(d.alpha, acc[i][j]);
+      double2* out = d.C + (size_t)r * ldc + c;
+      if (!zero_beta) v = cadd(v, cmul(d.beta, *out));
+      *out = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) zgemm_batched_kernel(const GemmDesc* __restrict__ descs) {
+  gemm_tile(descs[blockIdx.z]);
+}
+
+__global__ void __launch_bounds__(256) zgemm_small_kernel(const GemmBatch batch) {
+  gemm_tile(batch.d[blockIdx.z]);
+}
+
+}  // namespace
+
+void launch_zgemm_small(const GemmBatch& b, int max_m, int max_n, cudaStream_t st) {
+  if (b.count <= 0 || max_m <= 0 || max_n <= 0) return;
+  dim3 grid((max_n + TN - 1) / TN, (max_m + TM - 1) / TM, b.count);
+  zgemm_small_kernel<<<grid, 256, 0, st>>>(b);
+  note_launch();
+}
+
+void launch_zgemm_batched(const GemmDesc* d_descs, int count, int max_m, int max_n, cudaStream_t st) {
+  if (count <= 0 || max_m <= 0 || max_n <= 0) return;
+  dim3 grid((max_n + TN - 1) / TN, (max_m + TM - 1) / TM, count);
+  zgemm_batched_kernel<<<grid, 256, 0, st>>>(d_descs);
+  note_launch();
+}
+
+}  // namespace mpsk

@@ -1,0 +1,113 @@
+// Kernel launchers of libmps (internal).  All sizes that depend on truncation are read from
+// device memory (`dims`), so every launcher can be enqueued without a host synchronisation.
+//
+// dims layout of a state with n sites: dims[i], i = 0..n, is the dimension of the bond left
+// of site i (dims[0] = dims[n] = 1), so site s is B_s[dims[s]][2][dims[s+1]].  Schmidt vectors
+// use the same slot numbering: slot i holds lambda of the bond between sites i-1 and i, slot 0
+// is the trivial left boundary [1].
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mpsk {
+
+void note_launch();
+long long launches();
+
+void launch_zgemm_batched(const GemmDesc* d_descs, int count, int max_m, int max_n, cudaStream_t st);
+// up to 4 descriptors passed by value (no device-side descriptor storage needed)
+struct GemmBatch {
+  GemmDesc d[4];
+  int count;
+};
+void launch_zgemm_small(const GemmBatch& b, int max_m, int max_n, cudaStream_t st);
+
+// G (16 complex per gate) and dG/dphi from the gate table and theta (device).
+void launch_gate_matrices(const void* d_gates, int n_gates, const double* d_theta, int n_theta,
+                          double2* G, double2* dG, int* status, cudaStream_t st);
+
+// C[(a,i'),(j',c)] = sum_ij G[(i'j'),(ij)] sum_m B_b[a,i,m] B_{b+1}[m,j,c]  (row-major, optional)
+// A = lambda_{slot b} * C, column-major (input of the SVD).
+void launch_contract(const double2* Bl, const double2* Br, const int* dims, int b, const double2* G,
+                     const double* lam_left, double2* C, double2* A, int max_dl, int max_dr,
+                     cudaStream_t st);
+
+// One-sided Jacobi SVD of A (m x ncol, column-major) with V accumulated, sorted descending,
+// truncated (Sec. 3 rule).  Writes Vs (sorted V, column-major), s (ncol, zero padded),
+// lam_out (slot b+1), dims[b+1] = k, and when non-null: W (sorted A V), tape_dims
+// {Dl, Dm, Dr, k} and lam_left_copy (slot b copied).
+struct SvdArgs {
+  double2* A;
+  double2* Vw;
+  int* dims;
+  int b;
+  int D;
+  double eps;
+  double2* Vs;
+  double* s;
+  double* lam_out;
+  double2* W;
+  int* tape_dims;
+  const double* lam_left;
+  double* lam_left_copy;
+  int* status;
+};
+void launch_svd(const SvdArgs& a, cudaStream_t st);
+
+// B_{b+1} <- (Vs[:, :k])^H reshaped [k][2][Dr]
+void launch_vh_rows(const double2* Vs, const int* dims, int b, double2* Br_out, int max_k, int max_ncol,
+                    cudaStream_t st);
+
+// ---- gate adjoint pieces; `td` = tape dims {Dl, Dm, Dr, k} ------------------------------------
+void launch_conjT(const double2* Bbar_r, const int* td, double2* Vbar, int max_k, int max_ncol,
+                  cudaStream_t st);
+void launch_sbar(double* lambar_slot, const double* s, const int* td, double* wbar, int max_ncol,
+                 cudaStream_t st);
+void launch_build_K(const double2* Y, const double* s, const double* wbar, const int* td, double2* K,
+                    int max_ncol, cudaStream_t st);
+void launch_lam_scale(double2* Cbar, const double2* Ctbar, const double2* C, const double* lam_left,
+                      const int* td, double* lambar_left, int max_dl, cudaStream_t st);
+void launch_gbar(const double2* Cbar, const double2* Theta, const int* td, const double2* dG,
+                 double2* Gbar, double* gate_grad, cudaStream_t st);
+void launch_thetabar(const double2* Cbar, const double2* G, const int* td, double2* Thbar, int max_dl,
+                     int max_dr, cudaStream_t st);
+void launch_theta_reduce(const double* gate_grad, const int* csr_off, const int* csr_gate,
+                         const double* csr_scale, int n_theta, double* grad, cudaStream_t st);
+
+// ---- energy ----------------------------------------------------------------------------------
+// OB[ob_off[3s+o]] = O applied to the physical index of B_s, o = 0 X, 1 Y, 2 Z.
+void launch_apply_paulis(const double2* B, const size_t* site_off, const size_t* ob_off, const int* dims,
+                         int n, double2* OB, int max_site, cudaStream_t st);
+// e[t] = sum_{x,y} L_t[x][y] R_t[x][y] for pairs given by pointer tables; D from dims[didx[t]]
+void launch_env_dots(const double2* const* Ls, const double2* const* Rs, const int* didx, const int* dims,
+                     int count, double2* e, cudaStream_t st);
+// E = (sum_k c_k Re e_k) / Re Z with compensated (Neumaier) summation, deterministic order;
+// expect (optional) = Re e_k / Re Z.
+void launch_energy_sum(const double2* e, const double* c, int n_terms, double c0, const double2* Z,
+                       double* E_out, double* expect, int* status, cudaStream_t st);
+// Y[t] = sum over a list of sources (alpha_j * X_j), fixed order; used for trie reductions.
+struct AxpyList {
+  double2* out;
+  int src_begin, src_end;   // into the src tables
+  int didx;                 // element count = dims[didx]^2 * mult
+  int mult;
+  int accumulate;           // 1: out += ..., 0: out = ...
+};
+void launch_axpy_lists(const AxpyList* lists, int count, const double2* const* src, const double* src_coef,
+                       const int* dims, int max_elems, cudaStream_t st);
+// out = AR + (c0 - *E) * RI over dims[slot]^2 elements
+void launch_rsum(double2* out, const double2* AR, const double2* RI, double c0, const double* E, const int* dims,
+                 int slot, int max_elems, cudaStream_t st);
+// Bbar_s = (sum_nodes O_node . E_node + Eid) / Z for one site; node_op: 0 I, 1 X, 2 Y, 3 Z
+struct SeedSite {
+  double2* out;        // Bbar_s [Dl][2][Dr]
+  const double2* Eid;  // identity-part environment [Dl][2][Dr]
+  int node_begin, node_end;
+  int s;               // site
+};
+void launch_seed_assemble(const SeedSite* sites, int n_sites, const double2* const* Enode, const int* node_op,
+                          const int* dims, const double2* Z, int max_site, cudaStream_t st);
+
+}  // namespace mpsk

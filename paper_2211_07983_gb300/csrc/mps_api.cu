@@ -1,0 +1,1225 @@
+// libmps host engine and C ABI (see include/mps.h).
+//
+// Pipeline of one energy + gradient evaluation (all on the caller's stream, bond dimensions
+// kept on the device so nothing waits on the host between gates):
+//   1. gate matrices G(phi), dG/dphi from theta                         (gate_kernels.cu)
+//   2. forward: per gate contract -> Jacobi SVD + truncation -> update  (Sec. 3), MPS snapshot
+//      every `checkpoint_every` gates
+//   3. energy by trie-shared transfer sweeps, and its cotangent Bbar = dE/dB*  (Sec. 2-3; Sec. 4
+//      Eq. expecgrad)
+//   4. reverse: per segment, restore the snapshot, recompute with a tape, then run the exact
+//      adjoint of every gate backwards (Sec. 4, Eq. circuitevolvegrad; App. A rules)
+//   5. dE/dtheta = sum over the Rz angles that share a theta (fixed order)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+
+#include "engine.h"
+
+using namespace mpsk;
+
+namespace mpsk {
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launches() { return g_launches.load(); }
+}  // namespace mpsk
+
+namespace mpsi {
+
+static thread_local std::string g_err;
+
+mps_status fail(mps_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+void clear_error() { g_err.clear(); }
+
+mps_status DevBuf::alloc(size_t nbytes) {
+  reset();
+  if (nbytes == 0) nbytes = 16;
+  cudaError_t e = cudaMalloc(&p, nbytes);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    cudaGetLastError();
+    return fail(MPS_ENOMEM, "cudaMalloc(" + std::to_string(nbytes) + " bytes): " + cudaGetErrorString(e));
+  }
+  bytes = nbytes;
+  MPS_CU(cudaMemset(p, 0, nbytes));
+  return MPS_OK;
+}
+
+mps_status DevBuf::ensure(size_t nbytes) {
+  if (p && bytes >= nbytes) return MPS_OK;
+  return alloc(nbytes);
+}
+
+void Layout::build(int n_, int D_) {
+  n = n_;
+  D = D_;
+  cap.assign(n + 1, 1);
+  max_cap = 1;
+  for (int i = 1; i < n; ++i) {
+    int e = std::min(i, n - i);
+    long long c = e >= 30 ? (long long)D : std::min<long long>(1ll << e, D);
+    cap[i] = (int)c;
+    max_cap = std::max(max_cap, cap[i]);
+  }
+  site_off.assign(n + 1, 0);
+  for (int s = 0; s < n; ++s) site_off[s + 1] = site_off[s] + (size_t)cap[s] * 2 * cap[s + 1];
+  lam_off.assign(n + 2, 0);
+  for (int i = 0; i <= n; ++i) lam_off[i + 1] = lam_off[i] + (size_t)cap[i];
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+mps_status StateBuf::alloc(const Layout& L) {
+  size_t b1 = align256(L.site_elems() * sizeof(double2));
+  size_t b2 = align256(L.lam_elems() * sizeof(double));
+  size_t b3 = align256((L.n + 1) * sizeof(int));
+  MPS_TRY(mem.alloc(b1 + b2 + b3));
+  char* base = mem.as<char>();
+  B = reinterpret_cast<double2*>(base);
+  lam = reinterpret_cast<double*>(base + b1);
+  dims = reinterpret_cast<int*>(base + b1 + b2);
+  return MPS_OK;
+}
+
+mps_status StateBuf::copy_from(const StateBuf& o, const Layout& L, cudaStream_t st) {
+  (void)L;
+  MPS_CU(cudaMemcpyAsync(mem.p, o.mem.p, mem.bytes, cudaMemcpyDeviceToDevice, st));
+  return MPS_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a{};
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---- workspace ------------------------------------------------------------------------------
+struct TapeSlot {
+  double2 *Bl, *Br, *C, *W, *Vs;
+  double *s, *lamL;
+  int* dims;
+};
+
+struct Workspace {
+  DevBuf A, Vw, C, Vs, s;                         // forward scratch at the largest bond
+  DevBuf G, dG, theta, scalars, gate_grad, grad;  // per call
+  StateBuf work, rec;                             // energy_grad working states
+  std::vector<std::unique_ptr<StateBuf>> snaps;
+  DevBuf tape;
+  DevBuf Bbar, lambar;
+  DevBuf rv;                                      // reverse scratch
+  double2 *Vbar = nullptr, *Cbar = nullptr, *Y = nullptr, *Km = nullptr, *T1 = nullptr, *Ctbar = nullptr,
+          *Theta = nullptr, *Thbar = nullptr, *Gbar = nullptr;
+  double* wbar = nullptr;
+  bool work_ok = false;
+};
+
+struct Ctx {
+  const Layout* L;
+  const mps_config* cfg;
+  cudaStream_t st;
+  int* status;
+  Workspace* ws;
+};
+
+static mps_status ensure_forward_scratch(const Layout& L, Workspace& w) {
+  const size_t mc = 2 * (size_t)L.max_cap, nc = 2 * (size_t)L.max_cap;
+  MPS_TRY(w.A.ensure(mc * nc * sizeof(double2)));
+  MPS_TRY(w.Vw.ensure(nc * nc * sizeof(double2)));
+  MPS_TRY(w.C.ensure(mc * nc * sizeof(double2)));
+  MPS_TRY(w.Vs.ensure(nc * nc * sizeof(double2)));
+  MPS_TRY(w.s.ensure(nc * sizeof(double)));
+  return MPS_OK;
+}
+
+static GemmDesc make_desc(const int* dims, const double2* A, int opA, const double2* B, int opB, double2* C,
+                          DimExpr M, DimExpr N, DimExpr K, DimExpr lda, DimExpr ldb, DimExpr ldc,
+                          bool accumulate = false) {
+  GemmDesc d{};
+  d.A = A;
+  d.B = B;
+  d.C = C;
+  d.dims = dims;
+  d.M = M;
+  d.N = N;
+  d.K = K;
+  d.lda = lda;
+  d.ldb = ldb;
+  d.ldc = ldc;
+  d.opA = opA;
+  d.opB = opB;
+  d.alpha = make_double2(1.0, 0.0);
+  d.beta = make_double2(accumulate ? 1.0 : 0.0, 0.0);
+  return d;
+}
+
+// one gate on bond b: contract -> SVD/truncate -> update (Sec. 3); with a tape when `tp`
+static mps_status forward_gate(Ctx& cx, StateBuf& sb, int b, const double2* Gt, const TapeSlot* tp) {
+  const Layout& L = *cx.L;
+  Workspace& w = *cx.ws;
+  double2* Bl = sb.B + L.site_off[b];
+  double2* Br = sb.B + L.site_off[b + 1];
+  if (tp) {
+    MPS_CU(cudaMemcpyAsync(tp->Bl, Bl, L.site_cap(b) * sizeof(double2), cudaMemcpyDeviceToDevice, cx.st));
+    MPS_CU(cudaMemcpyAsync(tp->Br, Br, L.site_cap(b + 1) * sizeof(double2), cudaMemcpyDeviceToDevice, cx.st));
+  }
+  double2* C = tp ? tp->C : w.C.as<double2>();
+  double2* Vs = tp ? tp->Vs : w.Vs.as<double2>();
+  double* s = tp ? tp->s : w.s.as<double>();
+  launch_contract(Bl, Br, sb.dims, b, Gt, sb.lam + L.lam_off[b], C, w.A.as<double2>(), L.cap[b], L.cap[b + 2],
+                  cx.st);
+  SvdArgs a{};
+  a.A = w.A.as<double2>();
+  a.Vw = w.Vw.as<double2>();
+  a.dims = sb.dims;
+  a.b = b;
+  a.D = cx.cfg->max_bond;
+  a.eps = cx.cfg->cutoff;
+  a.Vs = Vs;
+  a.s = s;
+  a.lam_out = sb.lam + L.lam_off[b + 1];
+  a.W = tp ? tp->W : nullptr;
+  a.tape_dims = tp ? tp->dims : nullptr;
+  a.lam_left = sb.lam + L.lam_off[b];
+  a.lam_left_copy = tp ? tp->lamL : nullptr;
+  a.status = cx.status;
+  launch_svd(a, cx.st);
+  GemmBatch g{};
+  g.count = 1;
+  g.d[0] = make_desc(sb.dims, C, OP_N, Vs, OP_T, Bl, dref(b, 2), dref(b + 1), dref(b + 2, 2), dref(b + 2, 2),
+                     dref(b + 2, 2), dref(b + 1));
+  launch_zgemm_small(g, 2 * L.cap[b], L.cap[b + 1], cx.st);
+  launch_vh_rows(Vs, sb.dims, b, Br, L.cap[b + 1], 2 * L.cap[b + 2], cx.st);
+  return MPS_OK;
+}
+
+static mps_status forward_gates(Ctx& cx, StateBuf& sb, const mps_circuit* c, const double2* G, int g0, int g1,
+                                const std::vector<TapeSlot>* tapes) {
+  for (int t = g0; t < g1; ++t) {
+    const TapeSlot* tp = tapes ? &(*tapes)[t - g0] : nullptr;
+    MPS_TRY(forward_gate(cx, sb, c->host[t].bond, G + 16 * (size_t)t, tp));
+  }
+  MPS_CU(cudaGetLastError());
+  return MPS_OK;
+}
+
+// exact adjoint of one gate (Sec. 4 / App. A): cotangents of the gate's outputs
+// (Bbar_b, Bbar_{b+1}, lambar of bond b) -> cotangents of its inputs and dE/dphi.
+static mps_status reverse_gate(Ctx& cx, int t, int b, const TapeSlot& tp, double2* Bbar, double* lambar,
+                               const double2* G, const double2* dG, double* gate_grad) {
+  const Layout& L = *cx.L;
+  Workspace& w = *cx.ws;
+  const int* td = tp.dims;
+  const DimExpr m = dref(0, 2), Dm = dref(1), nc = dref(2, 2), k = dref(3);
+  double2* Bbl = Bbar + L.site_off[b];
+  double2* Bbr = Bbar + L.site_off[b + 1];
+  const int mcap = 2 * L.cap[b], ncap = 2 * L.cap[b + 2], kcap = L.cap[b + 1];
+  launch_conjT(Bbr, td, w.Vbar, kcap, ncap, cx.st);                          // Vbar = Bbar_{b+1}^H
+  GemmBatch g{};
+  g.count = 3;
+  g.d[0] = make_desc(td, tp.C, OP_H, Bbl, OP_N, w.Vbar, nc, k, m, nc, k, k, true);     // Vbar += C^H Bbar_b
+  g.d[1] = make_desc(td, Bbl, OP_N, tp.Vs, OP_C, w.Cbar, m, nc, k, k, nc, nc);         // Cbar = Bbar_b V_k^H
+  g.d[2] = make_desc(td, tp.Bl, OP_N, tp.Br, OP_N, w.Theta, m, nc, Dm, Dm, nc, nc);    // Theta = B_b B_{b+1}
+  launch_zgemm_small(g, std::max(mcap, ncap), std::max(kcap, ncap), cx.st);
+  launch_sbar(lambar + L.lam_off[b + 1], tp.s, td, w.wbar, ncap, cx.st);              // sbar -> wbar
+  g.count = 1;
+  g.d[0] = make_desc(td, tp.Vs, OP_C, w.Vbar, OP_N, w.Y, nc, k, nc, nc, k, k);         // Y = V^H Vbar
+  launch_zgemm_small(g, ncap, kcap, cx.st);
+  launch_build_K(w.Y, tp.s, w.wbar, td, w.Km, ncap, cx.st);                            // diag(wbar)+J+J^H
+  g.d[0] = make_desc(td, tp.W, OP_T, w.Km, OP_N, w.T1, m, nc, nc, m, nc, nc);           // T1 = (C~ V) K
+  launch_zgemm_small(g, mcap, ncap, cx.st);
+  g.d[0] = make_desc(td, w.T1, OP_N, tp.Vs, OP_C, w.Ctbar, m, nc, nc, nc, nc, nc);     // C~bar = T1 V^H
+  launch_zgemm_small(g, mcap, ncap, cx.st);
+  launch_lam_scale(w.Cbar, w.Ctbar, tp.C, tp.lamL, td, b > 0 ? lambar + L.lam_off[b] : nullptr, L.cap[b],
+                   cx.st);
+  launch_gbar(w.Cbar, w.Theta, td, dG + 16 * (size_t)t, w.Gbar, gate_grad + t, cx.st);
+  launch_thetabar(w.Cbar, G + 16 * (size_t)t, td, w.Thbar, L.cap[b], L.cap[b + 2], cx.st);
+  g.count = 2;
+  g.d[0] = make_desc(td, w.Thbar, OP_N, tp.Br, OP_H, Bbl, m, Dm, nc, nc, nc, Dm);      // Bbar_b = Thbar B_{b+1}^H
+  g.d[1] = make_desc(td, tp.Bl, OP_H, w.Thbar, OP_N, Bbr, Dm, nc, m, Dm, nc, nc);      // Bbar_{b+1} = B_b^H Thbar
+  launch_zgemm_small(g, std::max(mcap, kcap), std::max(kcap, ncap), cx.st);
+  return MPS_OK;
+}
+
+}  // namespace mpsi
+
+// ===================================================================================================
+// energy engine
+// ===================================================================================================
+namespace mpsi {
+
+struct Step {
+  enum Kind { GEMM, AXPY, PAULIS, DOTS, SUM, RSUM, SEED } kind;
+  int off = 0, count = 0, max_m = 0, max_n = 0;
+  int slot = 0;
+};
+
+struct EnergyCache {
+  const void* key_B = nullptr;
+  const int* key_dims = nullptr;
+  DevBuf bufs, tables;
+  std::vector<Step> plan_e, plan_seed;
+  // device views
+  GemmDesc* d_desc = nullptr;
+  AxpyList* d_axpy = nullptr;
+  const double2** d_src = nullptr;
+  double* d_srccoef = nullptr;
+  const double2** d_dotL = nullptr;
+  const double2** d_dotR = nullptr;
+  int* d_dotdidx = nullptr;
+  SeedSite* d_seed = nullptr;
+  const double2** d_Enode = nullptr;
+  int* d_nodeop = nullptr;
+  size_t* d_site_off = nullptr;
+  size_t* d_ob_off = nullptr;
+  double2* OB = nullptr;
+  double2* e = nullptr;
+  double2* Z = nullptr;
+  std::vector<double2*> RI, AR, Rsum;
+  int max_site = 1;
+};
+
+}  // namespace mpsi
+
+mps_hamiltonian_dev::~mps_hamiltonian_dev() = default;
+
+namespace mpsi {
+
+// Build every buffer, descriptor and step of the energy (+ cotangent) pass for one state layout.
+static mps_status build_energy_cache(const Layout& L, const StateBuf& sb, mps_hamiltonian_dev* h,
+                                     EnergyCache& ec) {
+  const int n = L.n;
+  const int nn = (int)h->node_site.size();
+  const int nt = (int)h->x.size();
+  const std::vector<int>& cap = L.cap;
+  auto sq = [&](int i) { return (size_t)cap[i] * cap[i]; };
+  auto site_sz = [&](int s) { return (size_t)cap[s] * 2 * cap[s + 1]; };
+  // ---- buffer plan (complex elements) ----
+  std::vector<size_t> off;
+  size_t total = 0;
+  auto take = [&](size_t elems) {
+    size_t o = total;
+    total += (elems + 15) & ~size_t(15);
+    return o;
+  };
+  size_t o_one = take(1), o_zero = take(1);
+  std::vector<size_t> oLI(n), oTL(n), oUR(n), oRI(n + 1), oTA(n), oAL(n), oAR(n + 1), oRsum(n + 1), oEid(n),
+      oOB(3 * n), oURa(n);
+  for (int s = 0; s < n; ++s) {
+    oLI[s] = take(sq(s + 1));
+    oTL[s] = take(site_sz(s));
+    oUR[s] = take(site_sz(s));
+    oRI[s] = take(sq(s));
+    oTA[s] = take(site_sz(s));
+    oAL[s] = take(sq(s + 1));
+    oAR[s] = take(sq(s));
+    oRsum[s] = take(sq(s));
+    oEid[s] = take(site_sz(s));
+    oURa[s] = take(site_sz(s));
+    for (int o = 0; o < 3; ++o) oOB[3 * s + o] = take(site_sz(s));
+  }
+  oRI[n] = o_one;
+  oAR[n] = take(1);
+  oRsum[n] = take(1);
+  std::vector<size_t> oL(nn), oX(nn), oE(nn), oU(nn), oY(nn), oT(nn, (size_t)-1);
+  std::vector<char> is_parent(nn, 0);
+  for (int v = 0; v < nn; ++v)
+    if (h->node_parent[v] >= 0) is_parent[h->node_parent[v]] = 1;
+  for (int v = 0; v < nn; ++v) {
+    int s = h->node_site[v];
+    oL[v] = take(sq(s + 1));
+    oX[v] = take(sq(s + 1));
+    oE[v] = take(site_sz(s));
+    oU[v] = take(site_sz(s));
+    oY[v] = take(sq(s));
+    if (is_parent[v] && s + 1 < n) oT[v] = take(site_sz(s + 1));
+  }
+  size_t o_e = take(2 * (size_t)std::max(nt, 1));
+  MPS_TRY(ec.bufs.alloc(total * sizeof(double2)));
+  double2* base = ec.bufs.as<double2>();
+  auto P = [&](size_t o) { return base + o; };
+  double2 one_val = make_double2(1.0, 0.0);
+  MPS_CU(cudaMemcpy(P(o_one), &one_val, sizeof(double2), cudaMemcpyHostToDevice));
+  ec.e = P(o_e);
+  ec.Z = P(oLI[n - 1]);
+  ec.OB = base;
+  ec.RI.resize(n + 1);
+  ec.AR.resize(n + 1);
+  ec.Rsum.resize(n + 1);
+  for (int s = 0; s <= n; ++s) {
+    ec.RI[s] = P(oRI[s]);
+    ec.AR[s] = P(oAR[s]);
+    ec.Rsum[s] = P(oRsum[s]);
+  }
+  ec.max_site = 1;
+  for (int s = 0; s < n; ++s) ec.max_site = std::max<int>(ec.max_site, cap[s] * cap[s + 1]);
+
+  // ---- descriptors and steps ----
+  std::vector<GemmDesc> D;
+  std::vector<AxpyList> AX;
+  std::vector<const double2*> SRC;
+  std::vector<double> SRCC;
+  const int* dims = sb.dims;
+  auto Bs = [&](int s) { return (const double2*)(sb.B + L.site_off[s]); };
+  auto OBp = [&](int s, int op) -> const double2* { return op == 0 ? Bs(s) : P(oOB[3 * s + op - 1]); };
+  auto gemm_step = [&](std::vector<Step>& plan, size_t first, int mm, int mn) {
+    Step st{Step::GEMM};
+    st.off = (int)first;
+    st.count = (int)(D.size() - first);
+    st.max_m = mm;
+    st.max_n = mn;
+    if (st.count > 0) plan.push_back(st);
+  };
+  auto axpy_step = [&](std::vector<Step>& plan, size_t first, int max_elems) {
+    Step st{Step::AXPY};
+    st.off = (int)first;
+    st.count = (int)(AX.size() - first);
+    st.max_m = max_elems;
+    if (st.count > 0) plan.push_back(st);
+  };
+  std::vector<Step>& PE = ec.plan_e;
+  std::vector<Step>& PS = ec.plan_seed;
+  PE.clear();
+  PS.clear();
+  PE.push_back(Step{Step::PAULIS});
+  // identity environments L^I (left) and R^I (right), interleaved two per launch
+  for (int q = 0; q < n; ++q) {
+    size_t f = D.size();
+    int s = q;   // left chain, first half-step: TL_s = L^I_{s-1} B_s
+    const double2* Lp = s == 0 ? P(o_one) : P(oLI[s - 1]);
+    D.push_back(make_desc(dims, Lp, OP_N, Bs(s), OP_N, P(oTL[s]), dref(s), dref(s + 1, 2), dref(s), dref(s),
+                          dref(s + 1, 2), dref(s + 1, 2)));
+    int r = n - 1 - q;   // right chain: UR_r = B_r R^I_{r+1}^T
+    D.push_back(make_desc(dims, Bs(r), OP_N, P(oRI[r + 1]), OP_T, P(oUR[r]), dref(r, 2), dref(r + 1),
+                          dref(r + 1), dref(r + 1), dref(r + 1), dref(r + 1)));
+    gemm_step(PE, f, std::max(cap[s], 2 * cap[r]), std::max(2 * cap[s + 1], cap[r + 1]));
+    f = D.size();
+    // L^I_s = B_s^H TL_s ; R^I_r = conj(B_r) UR_r^T
+    D.push_back(make_desc(dims, Bs(s), OP_H, P(oTL[s]), OP_N, P(oLI[s]), dref(s + 1), dref(s + 1), dref(s, 2),
+                          dref(s + 1), dref(s + 1), dref(s + 1)));
+    D.push_back(make_desc(dims, Bs(r), OP_C, P(oUR[r]), OP_T, P(oRI[r]), dref(r), dref(r), dref(r + 1, 2),
+                          dref(r + 1, 2), dref(r + 1, 2), dref(r)));
+    gemm_step(PE, f, std::max(cap[s + 1], cap[r]), std::max(cap[s + 1], cap[r]));
+  }
+  // trie forward sweep, site by site
+  auto Tpar = [&](int v) -> double2* {
+    int p = h->node_parent[v];
+    return p < 0 ? P(oTL[h->node_site[v]]) : P(oT[p]);
+  };
+  for (int s = 0; s < n; ++s) {
+    int v0 = h->site_begin[s], v1 = h->site_begin[s + 1];
+    if (v0 == v1) continue;
+    size_t f = D.size();
+    std::vector<char> done(nn, 0);
+    for (int v = v0; v < v1; ++v) {
+      int p = h->node_parent[v];
+      if (p < 0 || done[p]) continue;
+      done[p] = 1;
+      D.push_back(make_desc(dims, P(oL[p]), OP_N, Bs(s), OP_N, P(oT[p]), dref(s), dref(s + 1, 2), dref(s), dref(s),
+                            dref(s + 1, 2), dref(s + 1, 2)));
+    }
+    gemm_step(PE, f, cap[s], 2 * cap[s + 1]);
+    f = D.size();
+    for (int v = v0; v < v1; ++v)
+      D.push_back(make_desc(dims, OBp(s, h->node_op[v]), OP_H, Tpar(v), OP_N, P(oL[v]), dref(s + 1), dref(s + 1),
+                            dref(s, 2), dref(s + 1), dref(s + 1), dref(s + 1)));
+    gemm_step(PE, f, cap[s + 1], cap[s + 1]);
+  }
+  // string expectations and the energy
+  std::vector<const double2*> dotL(nt), dotR(nt);
+  std::vector<int> dotd(nt);
+  for (int k = 0; k < nt; ++k) {
+    int v = h->term_node[k];
+    int b = h->node_site[v];
+    dotL[k] = P(oL[v]);
+    dotR[k] = P(oRI[b + 1]);
+    dotd[k] = b + 1;
+  }
+  PE.push_back(Step{Step::DOTS});
+  PE.push_back(Step{Step::SUM});
+
+  // ---- cotangent ----
+  // X_v = c_v R^I_{s+1} + sum_children Y_child;  Y_c = T^R_{O_c}(X_c)
+  for (int t = n - 1; t >= 0; --t) {
+    int v0 = h->site_begin[t], v1 = h->site_begin[t + 1];
+    if (v0 == v1) continue;
+    size_t fa = AX.size();
+    for (int v = v0; v < v1; ++v) {
+      AxpyList a{};
+      a.out = P(oX[v]);
+      a.src_begin = (int)SRC.size();
+      if (h->node_is_end[v]) {
+        SRC.push_back(P(oRI[t + 1]));
+        SRCC.push_back(h->node_end_coeff[v]);
+      }
+      for (int e = h->child_off[v]; e < h->child_off[v + 1]; ++e) {
+        SRC.push_back(P(oY[h->child_idx[e]]));
+        SRCC.push_back(1.0);
+      }
+      a.src_end = (int)SRC.size();
+      a.didx = t + 1;
+      a.mult = 1;
+      a.accumulate = 0;
+      AX.push_back(a);
+    }
+    axpy_step(PS, fa, cap[t + 1] * cap[t + 1]);
+    if (t == 0) continue;
+    size_t f = D.size();
+    for (int v = v0; v < v1; ++v)
+      D.push_back(make_desc(dims, Bs(t), OP_N, P(oX[v]), OP_T, P(oU[v]), dref(t, 2), dref(t + 1), dref(t + 1),
+                            dref(t + 1), dref(t + 1), dref(t + 1)));
+    gemm_step(PS, f, 2 * cap[t], cap[t + 1]);
+    f = D.size();
+    for (int v = v0; v < v1; ++v)
+      D.push_back(make_desc(dims, OBp(t, h->node_op[v]), OP_C, P(oU[v]), OP_T, P(oY[v]), dref(t), dref(t),
+                            dref(t + 1, 2), dref(t + 1, 2), dref(t + 1, 2), dref(t)));
+    gemm_step(PS, f, cap[t], cap[t]);
+  }
+  // A^R_t = T^R_I(A^R_{t+1}) + sum_{roots at t} Y_root,  t = n-1 .. 1 (A^R_n = 0)
+  for (int t = n - 1; t >= 1; --t) {
+    size_t f = D.size();
+    D.push_back(make_desc(dims, Bs(t), OP_N, P(oAR[t + 1]), OP_T, P(oURa[t]), dref(t, 2), dref(t + 1), dref(t + 1),
+                          dref(t + 1), dref(t + 1), dref(t + 1)));
+    gemm_step(PS, f, 2 * cap[t], cap[t + 1]);
+    f = D.size();
+    D.push_back(make_desc(dims, Bs(t), OP_C, P(oURa[t]), OP_T, P(oAR[t]), dref(t), dref(t), dref(t + 1, 2),
+                          dref(t + 1, 2), dref(t + 1, 2), dref(t)));
+    gemm_step(PS, f, cap[t], cap[t]);
+    size_t fa = AX.size();
+    AxpyList a{};
+    a.out = P(oAR[t]);
+    a.src_begin = (int)SRC.size();
+    for (int v = h->site_begin[t]; v < h->site_begin[t + 1]; ++v)
+      if (h->node_parent[v] < 0) {
+        SRC.push_back(P(oY[v]));
+        SRCC.push_back(1.0);
+      }
+    a.src_end = (int)SRC.size();
+    a.didx = t;
+    a.mult = 1;
+    a.accumulate = 1;
+    if (a.src_end > a.src_begin) AX.push_back(a);
+    axpy_step(PS, fa, cap[t] * cap[t]);
+  }
+  // A^L_s = T_I(A^L_{s-1}) + sum_{strings ending at s} c L_leaf;  TA_s = A^L_{s-1} B_s
+  for (int s = 0; s < n; ++s) {
+    size_t f = D.size();
+    const double2* Ap = s == 0 ? P(o_zero) : P(oAL[s - 1]);
+    D.push_back(make_desc(dims, Ap, OP_N, Bs(s), OP_N, P(oTA[s]), dref(s), dref(s + 1, 2), dref(s), dref(s),
+                          dref(s + 1, 2), dref(s + 1, 2)));
+    gemm_step(PS, f, cap[s], 2 * cap[s + 1]);
+    if (s == n - 1) break;
+    f = D.size();
+    D.push_back(make_desc(dims, Bs(s), OP_H, P(oTA[s]), OP_N, P(oAL[s]), dref(s + 1), dref(s + 1), dref(s, 2),
+                          dref(s + 1), dref(s + 1), dref(s + 1)));
+    gemm_step(PS, f, cap[s + 1], cap[s + 1]);
+    size_t fa = AX.size();
+    AxpyList a{};
+    a.out = P(oAL[s]);
+    a.src_begin = (int)SRC.size();
+    for (int v = h->site_begin[s]; v < h->site_begin[s + 1]; ++v)
+      if (h->node_is_end[v]) {
+        SRC.push_back(P(oL[v]));
+        SRCC.push_back(h->node_end_coeff[v]);
+      }
+    a.src_end = (int)SRC.size();
+    a.didx = s + 1;
+    a.mult = 1;
+    a.accumulate = 1;
+    if (a.src_end > a.src_begin) AX.push_back(a);
+    axpy_step(PS, fa, cap[s + 1] * cap[s + 1]);
+  }
+  // Rsum_s = A^R_s + (c0 - E) R^I_s
+  for (int s = 1; s <= n; ++s) {
+    Step st{Step::RSUM};
+    st.slot = s;
+    st.max_m = cap[s] * cap[s];
+    PS.push_back(st);
+  }
+  // Eid_s = TA_s R^I_{s+1}^T + TL_s Rsum_{s+1}^T
+  {
+    size_t f = D.size();
+    int mm = 1, mn = 1;
+    for (int s = 0; s < n; ++s) {
+      D.push_back(make_desc(dims, P(oTA[s]), OP_N, P(oRI[s + 1]), OP_T, P(oEid[s]), dref(s, 2), dref(s + 1),
+                            dref(s + 1), dref(s + 1), dref(s + 1), dref(s + 1)));
+      mm = std::max(mm, 2 * cap[s]);
+      mn = std::max(mn, cap[s + 1]);
+    }
+    gemm_step(PS, f, mm, mn);
+    f = D.size();
+    for (int s = 0; s < n; ++s)
+      D.push_back(make_desc(dims, P(oTL[s]), OP_N, P(oRsum[s + 1]), OP_T, P(oEid[s]), dref(s, 2), dref(s + 1),
+                            dref(s + 1), dref(s + 1), dref(s + 1), dref(s + 1), true));
+    gemm_step(PS, f, mm, mn);
+    // E_v = T_par(v) X_v^T for every node
+    f = D.size();
+    for (int v = 0; v < nn; ++v) {
+      int s = h->node_site[v];
+      D.push_back(make_desc(dims, Tpar(v), OP_N, P(oX[v]), OP_T, P(oE[v]), dref(s, 2), dref(s + 1), dref(s + 1),
+                            dref(s + 1), dref(s + 1), dref(s + 1)));
+    }
+    // launched in chunks of 65535 (grid z limit)
+    for (size_t c0 = f; c0 < D.size(); c0 += 65535) {
+      Step st{Step::GEMM};
+      st.off = (int)c0;
+      st.count = (int)std::min<size_t>(65535, D.size() - c0);
+      st.max_m = mm;
+      st.max_n = mn;
+      PS.push_back(st);
+    }
+  }
+  PS.push_back(Step{Step::SEED});
+  std::vector<SeedSite> seeds(n);
+  std::vector<const double2*> Enode(nn);
+  for (int v = 0; v < nn; ++v) Enode[v] = P(oE[v]);
+  for (int s = 0; s < n; ++s) {
+    seeds[s].out = nullptr;   // patched per call
+    seeds[s].Eid = P(oEid[s]);
+    seeds[s].node_begin = h->site_begin[s];
+    seeds[s].node_end = h->site_begin[s + 1];
+    seeds[s].s = s;
+  }
+  std::vector<size_t> ob_off(3 * n);
+  for (int i = 0; i < 3 * n; ++i) ob_off[i] = oOB[i];
+  // ---- upload tables ----
+  size_t tb = 0;
+  auto tk = [&](size_t bytes) {
+    size_t o = tb;
+    tb += align256(std::max<size_t>(bytes, 16));
+    return o;
+  };
+  size_t t_desc = tk(D.size() * sizeof(GemmDesc)), t_ax = tk(AX.size() * sizeof(AxpyList)),
+         t_src = tk(SRC.size() * sizeof(void*)), t_srcc = tk(SRCC.size() * sizeof(double)),
+         t_dl = tk(nt * sizeof(void*)), t_dr = tk(nt * sizeof(void*)), t_dd = tk(nt * sizeof(int)),
+         t_seed = tk(n * sizeof(SeedSite)), t_en = tk(nn * sizeof(void*)), t_op = tk(nn * sizeof(int)),
+         t_so = tk((n + 1) * sizeof(size_t)), t_ob = tk(3 * n * sizeof(size_t));
+  MPS_TRY(ec.tables.alloc(tb));
+  char* tbase = ec.tables.as<char>();
+  auto up = [&](size_t o, const void* src, size_t bytes) -> mps_status {
+    if (bytes) MPS_CU(cudaMemcpy(tbase + o, src, bytes, cudaMemcpyHostToDevice));
+    return MPS_OK;
+  };
+  MPS_TRY(up(t_desc, D.data(), D.size() * sizeof(GemmDesc)));
+  MPS_TRY(up(t_ax, AX.data(), AX.size() * sizeof(AxpyList)));
+  MPS_TRY(up(t_src, SRC.data(), SRC.size() * sizeof(void*)));
+  MPS_TRY(up(t_srcc, SRCC.data(), SRCC.size() * sizeof(double)));
+  MPS_TRY(up(t_dl, dotL.data(), nt * sizeof(void*)));
+  MPS_TRY(up(t_dr, dotR.data(), nt * sizeof(void*)));
+  MPS_TRY(up(t_dd, dotd.data(), nt * sizeof(int)));
+  MPS_TRY(up(t_seed, seeds.data(), n * sizeof(SeedSite)));
+  MPS_TRY(up(t_en, Enode.data(), nn * sizeof(void*)));
+  MPS_TRY(up(t_op, h->node_op.data(), nn * sizeof(int)));
+  MPS_TRY(up(t_so, L.site_off.data(), (n + 1) * sizeof(size_t)));
+  MPS_TRY(up(t_ob, ob_off.data(), 3 * n * sizeof(size_t)));
+  ec.d_desc = reinterpret_cast<GemmDesc*>(tbase + t_desc);
+  ec.d_axpy = reinterpret_cast<AxpyList*>(tbase + t_ax);
+  ec.d_src = reinterpret_cast<const double2**>(tbase + t_src);
+  ec.d_srccoef = reinterpret_cast<double*>(tbase + t_srcc);
+  ec.d_dotL = reinterpret_cast<const double2**>(tbase + t_dl);
+  ec.d_dotR = reinterpret_cast<const double2**>(tbase + t_dr);
+  ec.d_dotdidx = reinterpret_cast<int*>(tbase + t_dd);
+  ec.d_seed = reinterpret_cast<SeedSite*>(tbase + t_seed);
+  ec.d_Enode = reinterpret_cast<const double2**>(tbase + t_en);
+  ec.d_nodeop = reinterpret_cast<int*>(tbase + t_op);
+  ec.d_site_off = reinterpret_cast<size_t*>(tbase + t_so);
+  ec.d_ob_off = reinterpret_cast<size_t*>(tbase + t_ob);
+  ec.key_B = sb.B;
+  ec.key_dims = sb.dims;
+  return MPS_OK;
+}
+
+// Energy (and, when d_Bbar != null, the cotangent dE/dB* written in the state's site layout).
+static mps_status energy_pass_impl(const Layout& L, const StateBuf& sb, cudaStream_t st, int* status,
+                                   mps_hamiltonian_dev* h, double* d_E, double* d_expect, double2* d_Bbar) {
+  if (!h->cache || h->cache->key_B != sb.B || h->cache->key_dims != sb.dims) {
+    MPS_CU(cudaStreamSynchronize(st));
+    h->cache.reset(new EnergyCache());
+    MPS_TRY(build_energy_cache(L, sb, h, *h->cache));
+  }
+  EnergyCache& ec = *h->cache;
+  const int nt = (int)h->x.size();
+  auto run = [&](const std::vector<Step>& plan) -> mps_status {
+    for (const Step& s : plan) {
+      switch (s.kind) {
+        case Step::GEMM: launch_zgemm_batched(ec.d_desc + s.off, s.count, s.max_m, s.max_n, st); break;
+        case Step::AXPY:
+          launch_axpy_lists(ec.d_axpy + s.off, s.count, ec.d_src, ec.d_srccoef, sb.dims, s.max_m, st);
+          break;
+        case Step::PAULIS:
+          launch_apply_paulis(sb.B, ec.d_site_off, ec.d_ob_off, sb.dims, L.n, ec.OB, ec.max_site, st);
+          break;
+        case Step::DOTS: launch_env_dots(ec.d_dotL, ec.d_dotR, ec.d_dotdidx, sb.dims, nt, ec.e, st); break;
+        case Step::SUM:
+          launch_energy_sum(ec.e, h->d_coeff.as<double>(), nt, h->c0, ec.Z, d_E, d_expect, status, st);
+          break;
+        case Step::RSUM:
+          launch_rsum(ec.Rsum[s.slot], ec.AR[s.slot], ec.RI[s.slot], h->c0, d_E, sb.dims, s.slot, s.max_m, st);
+          break;
+        case Step::SEED: {
+          std::vector<SeedSite> seeds(L.n);
+          MPS_CU(cudaMemcpyAsync(seeds.data(), ec.d_seed, L.n * sizeof(SeedSite), cudaMemcpyDeviceToHost, st));
+          MPS_CU(cudaStreamSynchronize(st));
+          bool patch = false;
+          for (int q = 0; q < L.n; ++q)
+            if (seeds[q].out != d_Bbar + L.site_off[q]) {
+              seeds[q].out = d_Bbar + L.site_off[q];
+              patch = true;
+            }
+          if (patch)
+            MPS_CU(cudaMemcpyAsync(ec.d_seed, seeds.data(), L.n * sizeof(SeedSite), cudaMemcpyHostToDevice, st));
+          launch_seed_assemble(ec.d_seed, L.n, ec.d_Enode, ec.d_nodeop, sb.dims, ec.Z, ec.max_site, st);
+          break;
+        }
+      }
+    }
+    MPS_CU(cudaGetLastError());
+    return MPS_OK;
+  };
+  MPS_TRY(run(ec.plan_e));
+  if (d_Bbar) MPS_TRY(run(ec.plan_seed));
+  return MPS_OK;
+}
+
+// ---- hamiltonian upload: canonical order + trie ------------------------------------------
+static int first_site(uint64_t x, uint64_t z) {
+  uint64_t s = x | z;
+  return s ? __builtin_ctzll(s) : -1;
+}
+static int last_site(uint64_t x, uint64_t z) {
+  uint64_t s = x | z;
+  return s ? 63 - __builtin_clzll(s) : -1;
+}
+static int sym(uint64_t x, uint64_t z, int s) {
+  int xb = (x >> s) & 1, zb = (z >> s) & 1;
+  return xb ? (zb ? 2 : 1) : (zb ? 3 : 0);
+}
+
+static mps_status build_trie(mps_hamiltonian_dev* h) {
+  const int n = h->n;
+  const int nt = (int)h->x.size();
+  // DFS order over the canonically sorted strings: reuse the longest common prefix
+  std::vector<int> site, op, parent, is_end;
+  std::vector<double> endc;
+  h->term_node.assign(nt, -1);
+  std::vector<int> path;  // node ids of the previous string's path
+  int prev_a = -2;
+  for (int k = 0; k < nt; ++k) {
+    uint64_t x = h->x[k], z = h->z[k];
+    int a = first_site(x, z), b = last_site(x, z);
+    int lcp = 0;
+    if (a == prev_a) {
+      while (lcp < (int)path.size() && a + lcp <= b && op[path[lcp]] == sym(x, z, a + lcp)) ++lcp;
+    }
+    path.resize(lcp);
+    for (int s = a + lcp; s <= b; ++s) {
+      site.push_back(s);
+      op.push_back(sym(x, z, s));
+      parent.push_back(path.empty() ? -1 : path.back());
+      is_end.push_back(0);
+      endc.push_back(0.0);
+      path.push_back((int)site.size() - 1);
+    }
+    int leaf = path[b - a];
+    if (is_end[leaf]) return fail(MPS_EINVAL, "mps_hamiltonian_create: duplicate Pauli string");
+    is_end[leaf] = 1;
+    endc[leaf] = h->c[k];
+    h->term_node[k] = leaf;
+    path.resize(b - a + 1);
+    prev_a = a;
+  }
+  // stable sort nodes by site
+  const int nn = (int)site.size();
+  std::vector<int> order(nn);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return site[u] < site[v]; });
+  std::vector<int> newid(nn);
+  for (int i = 0; i < nn; ++i) newid[order[i]] = i;
+  h->node_site.resize(nn);
+  h->node_op.resize(nn);
+  h->node_parent.resize(nn);
+  h->node_is_end.resize(nn);
+  h->node_end_coeff.resize(nn);
+  for (int i = 0; i < nn; ++i) {
+    int u = order[i];
+    h->node_site[i] = site[u];
+    h->node_op[i] = op[u];
+    h->node_parent[i] = parent[u] < 0 ? -1 : newid[parent[u]];
+    h->node_is_end[i] = is_end[u];
+    h->node_end_coeff[i] = endc[u];
+  }
+  for (int k = 0; k < nt; ++k) h->term_node[k] = newid[h->term_node[k]];
+  h->site_begin.assign(n + 1, 0);
+  for (int i = 0; i < nn; ++i) h->site_begin[h->node_site[i] + 1]++;
+  for (int s = 0; s < n; ++s) h->site_begin[s + 1] += h->site_begin[s];
+  h->child_off.assign(nn + 1, 0);
+  for (int i = 0; i < nn; ++i)
+    if (h->node_parent[i] >= 0) h->child_off[h->node_parent[i] + 1]++;
+  for (int i = 0; i < nn; ++i) h->child_off[i + 1] += h->child_off[i];
+  h->child_idx.assign(h->child_off[nn], 0);
+  std::vector<int> fill(h->child_off.begin(), h->child_off.end() - 1);
+  for (int i = 0; i < nn; ++i)
+    if (h->node_parent[i] >= 0) h->child_idx[fill[h->node_parent[i]]++] = i;
+  return MPS_OK;
+}
+
+mps_status check_status_word(cudaStream_t st, DevBuf& status, const char* where) {
+  MPS_CU(cudaStreamSynchronize(st));
+  int code = 0;
+  MPS_CU(cudaMemcpy(&code, status.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (code != 0) {
+    MPS_CU(cudaMemset(status.p, 0, sizeof(int)));
+    const char* what = code == MPS_ENOCONV   ? "Jacobi SVD did not converge"
+                       : code == MPS_ENUMERIC ? "non-finite or zero norm met on the device"
+                       : code == MPS_EINVAL   ? "invalid angle index or non-finite angle"
+                                              : "device error";
+    return fail((mps_status)code, std::string(where) + ": " + what);
+  }
+  return MPS_OK;
+}
+
+static mps_status validate_config(const mps_config* cfg) {
+  if (!cfg) return fail(MPS_EINVAL, "config is NULL");
+  if (cfg->max_bond < 1 || cfg->max_bond > 256)
+    return fail(MPS_EINVAL, "max_bond must be in 1..256");
+  if (!(cfg->cutoff >= 0.0) || !std::isfinite(cfg->cutoff)) return fail(MPS_EINVAL, "cutoff must be finite and >= 0");
+  if (cfg->precision != MPS_PRECISION_FP64) return fail(MPS_EINVAL, "precision: only MPS_PRECISION_FP64 is built");
+  if (cfg->checkpoint_every < 0) return fail(MPS_EINVAL, "checkpoint_every must be >= 0");
+  return MPS_OK;
+}
+
+// theta (host or device) -> device copy in the workspace
+static mps_status stage_theta(mps_state* s, const double* theta, int n_theta, const double** d_theta) {
+  Workspace& w = *s->ws;
+  if (n_theta < 0) return fail(MPS_EINVAL, "n_theta < 0");
+  if (n_theta > 0 && !theta) return fail(MPS_EINVAL, "theta is NULL");
+  MPS_TRY(w.theta.ensure(std::max(1, n_theta) * sizeof(double)));
+  if (n_theta == 0) {
+    *d_theta = w.theta.as<double>();
+    return MPS_OK;
+  }
+  if (is_device_ptr(theta)) {
+    *d_theta = theta;   // finiteness is checked by the gate-matrix kernel
+    return MPS_OK;
+  }
+  for (int i = 0; i < n_theta; ++i)
+    if (!std::isfinite(theta[i])) return fail(MPS_EINVAL, "theta contains a non-finite value");
+  MPS_CU(cudaMemcpyAsync(w.theta.p, theta, n_theta * sizeof(double), cudaMemcpyHostToDevice, s->st));
+  *d_theta = w.theta.as<double>();
+  return MPS_OK;
+}
+
+static mps_status put_out(double* dst, const double* dsrc, size_t count, cudaStream_t st) {
+  if (!dst || count == 0) return MPS_OK;
+  MPS_CU(cudaMemcpyAsync(dst, dsrc, count * sizeof(double),
+                         is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  return MPS_OK;
+}
+
+static mps_status gate_matrices(mps_state* s, const mps_circuit* c, const double* d_theta, int n_theta) {
+  Workspace& w = *s->ws;
+  MPS_TRY(w.G.ensure(std::max(1, c->n_gates) * 16 * sizeof(double2)));
+  MPS_TRY(w.dG.ensure(std::max(1, c->n_gates) * 16 * sizeof(double2)));
+  launch_gate_matrices(c->gates.p, c->n_gates, d_theta, n_theta, w.G.as<double2>(), w.dG.as<double2>(),
+                       s->status.as<int>(), s->st);
+  return MPS_OK;
+}
+
+static mps_status check_circuit(const mps_state* s, const mps_circuit* c, int n_theta) {
+  if (!c) return fail(MPS_EINVAL, "circuit is NULL");
+  if (c->n != s->L.n) return fail(MPS_EINVAL, "circuit and state have different qubit counts");
+  if (c->max_theta_idx >= n_theta) return fail(MPS_EINVAL, "a gate's theta_idx is >= n_theta");
+  return MPS_OK;
+}
+
+}  // namespace mpsi
+
+using namespace mpsi;
+
+// ===================================================================================================
+// C ABI
+// ===================================================================================================
+extern "C" {
+
+const char* mps_last_error(void) { return mpsi::g_err.c_str(); }
+
+int64_t mps_kernel_launches(void) { return (int64_t)mpsk::launches(); }
+
+mps_status mps_init_product(int32_t n_qubits, const uint8_t* bits, const mps_config* cfg, mps_state** out) {
+  clear_error();
+  if (!out) return fail(MPS_EINVAL, "mps_init_product: out is NULL");
+  if (n_qubits < 2 || n_qubits > 64) return fail(MPS_EINVAL, "mps_init_product: n_qubits must be in 2..64");
+  if (!bits) return fail(MPS_EINVAL, "mps_init_product: bits is NULL");
+  MPS_TRY(validate_config(cfg));
+  for (int i = 0; i < n_qubits; ++i)
+    if (bits[i] > 1) return fail(MPS_EINVAL, "mps_init_product: bits must be 0 or 1");
+  std::unique_ptr<mps_state> s(new mps_state());
+  s->cfg = *cfg;
+  if (s->cfg.checkpoint_every == 0) s->cfg.checkpoint_every = 512;
+  s->st = (cudaStream_t)cfg->cuda_stream;
+  s->L.build(n_qubits, cfg->max_bond);
+  s->ws.reset(new Workspace());
+  MPS_TRY(s->buf.alloc(s->L));
+  MPS_TRY(s->status.alloc(sizeof(int)));
+  const Layout& L = s->L;
+  std::vector<double2> hB(L.site_elems(), make_double2(0.0, 0.0));
+  std::vector<double> hl(L.lam_elems(), 0.0);
+  std::vector<int> hd(n_qubits + 1, 1);
+  for (int q = 0; q < n_qubits; ++q) hB[L.site_off[q] + bits[q]] = make_double2(1.0, 0.0);   // [1][2][1]
+  for (int i = 0; i <= n_qubits; ++i) hl[L.lam_off[i]] = 1.0;
+  MPS_CU(cudaMemcpy(s->buf.B, hB.data(), hB.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  MPS_CU(cudaMemcpy(s->buf.lam, hl.data(), hl.size() * sizeof(double), cudaMemcpyHostToDevice));
+  MPS_CU(cudaMemcpy(s->buf.dims, hd.data(), hd.size() * sizeof(int), cudaMemcpyHostToDevice));
+  *out = s.release();
+  return MPS_OK;
+}
+
+mps_status mps_clone(const mps_state* s, mps_state** out) {
+  clear_error();
+  if (!s || !out) return fail(MPS_EINVAL, "mps_clone: NULL argument");
+  std::unique_ptr<mps_state> c(new mps_state());
+  c->cfg = s->cfg;
+  c->st = s->st;
+  c->L = s->L;
+  c->ws.reset(new Workspace());
+  MPS_TRY(c->buf.alloc(c->L));
+  MPS_TRY(c->status.alloc(sizeof(int)));
+  MPS_TRY(c->buf.copy_from(s->buf, s->L, s->st));
+  MPS_CU(cudaStreamSynchronize(s->st));
+  *out = c.release();
+  return MPS_OK;
+}
+
+void mps_free(mps_state* s) {
+  if (!s) return;
+  if (s->st) cudaStreamSynchronize(s->st);
+  else cudaDeviceSynchronize();
+  delete s;
+}
+
+mps_status mps_read_state(const mps_state* s, int32_t* dims, double* lam, double* tensors) {
+  clear_error();
+  if (!s || !dims) return fail(MPS_EINVAL, "mps_read_state: NULL argument");
+  const Layout& L = s->L;
+  MPS_CU(cudaStreamSynchronize(s->st));
+  std::vector<int> d(L.n + 1);
+  MPS_CU(cudaMemcpy(d.data(), s->buf.dims, (L.n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+  std::memcpy(dims, d.data(), (L.n + 1) * sizeof(int));
+  if (lam) {
+    size_t o = 0;
+    for (int i = 1; i < L.n; ++i) {
+      MPS_CU(cudaMemcpy(lam + o, s->buf.lam + L.lam_off[i], d[i] * sizeof(double), cudaMemcpyDeviceToHost));
+      o += d[i];
+    }
+  }
+  if (tensors) {
+    size_t o = 0;
+    for (int q = 0; q < L.n; ++q) {
+      size_t e = (size_t)d[q] * 2 * d[q + 1];
+      MPS_CU(cudaMemcpy(tensors + 2 * o, s->buf.B + L.site_off[q], e * sizeof(double2), cudaMemcpyDeviceToHost));
+      o += e;
+    }
+  }
+  return MPS_OK;
+}
+
+mps_status mps_circuit_create(int32_t n_qubits, const mps_gate* gates, int32_t n_gates, mps_circuit** out) {
+  clear_error();
+  if (!out) return fail(MPS_EINVAL, "mps_circuit_create: out is NULL");
+  if (n_qubits < 2 || n_qubits > 64) return fail(MPS_EINVAL, "mps_circuit_create: n_qubits must be in 2..64");
+  if (n_gates < 0 || (n_gates > 0 && !gates)) return fail(MPS_EINVAL, "mps_circuit_create: bad gate array");
+  std::unique_ptr<mps_circuit> c(new mps_circuit());
+  c->n = n_qubits;
+  c->n_gates = n_gates;
+  c->host.assign(gates, gates + n_gates);
+  for (int t = 0; t < n_gates; ++t) {
+    const mps_gate& g = gates[t];
+    if (g.bond < 0 || g.bond > n_qubits - 2)
+      return fail(MPS_EINVAL, "mps_circuit_create: gate " + std::to_string(t) + " bond out of range");
+    if (g.theta_idx >= 0 && (g.rz_site < 0 || g.rz_site > 1 || !std::isfinite(g.theta_scale)))
+      return fail(MPS_EINVAL, "mps_circuit_create: gate " + std::to_string(t) + " has a bad Rz description");
+    const double* arrs[3] = {g.mat, g.pre, g.post};
+    for (int q = 0; q < 3; ++q)
+      for (int e = 0; e < 32; ++e)
+        if (!std::isfinite(arrs[q][e])) return fail(MPS_EINVAL, "mps_circuit_create: non-finite gate matrix");
+    c->max_theta_idx = std::max(c->max_theta_idx, g.theta_idx);
+  }
+  MPS_TRY(c->gates.alloc(std::max(1, n_gates) * sizeof(mps_gate)));
+  if (n_gates) MPS_CU(cudaMemcpy(c->gates.p, gates, n_gates * sizeof(mps_gate), cudaMemcpyHostToDevice));
+  const int nth = c->max_theta_idx + 1;
+  std::vector<int> off(nth + 1, 0), gi;
+  std::vector<double> sc;
+  for (int t = 0; t < n_gates; ++t)
+    if (gates[t].theta_idx >= 0) off[gates[t].theta_idx + 1]++;
+  for (int i = 0; i < nth; ++i) off[i + 1] += off[i];
+  gi.assign(off[nth], 0);
+  sc.assign(off[nth], 0.0);
+  std::vector<int> fill(off.begin(), off.end() - 1);
+  for (int t = 0; t < n_gates; ++t)   // gate order inside each theta: fixed, ascending
+    if (gates[t].theta_idx >= 0) {
+      int p = fill[gates[t].theta_idx]++;
+      gi[p] = t;
+      sc[p] = gates[t].theta_scale;
+    }
+  MPS_TRY(c->csr_off.alloc((nth + 1) * sizeof(int)));
+  MPS_TRY(c->csr_gate.alloc(std::max<size_t>(1, gi.size()) * sizeof(int)));
+  MPS_TRY(c->csr_scale.alloc(std::max<size_t>(1, sc.size()) * sizeof(double)));
+  MPS_CU(cudaMemcpy(c->csr_off.p, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (!gi.empty()) {
+    MPS_CU(cudaMemcpy(c->csr_gate.p, gi.data(), gi.size() * sizeof(int), cudaMemcpyHostToDevice));
+    MPS_CU(cudaMemcpy(c->csr_scale.p, sc.data(), sc.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  *out = c.release();
+  return MPS_OK;
+}
+
+void mps_circuit_free(mps_circuit* c) { delete c; }
+
+mps_status mps_hamiltonian_create(int32_t n_qubits, const mps_hamiltonian* hin, mps_hamiltonian_dev** out) {
+  clear_error();
+  if (!out || !hin) return fail(MPS_EINVAL, "mps_hamiltonian_create: NULL argument");
+  if (n_qubits < 2 || n_qubits > 64) return fail(MPS_EINVAL, "mps_hamiltonian_create: n_qubits must be in 2..64");
+  if (hin->n_terms < 0 || (hin->n_terms > 0 && (!hin->x_mask || !hin->z_mask || !hin->coeff)))
+    return fail(MPS_EINVAL, "mps_hamiltonian_create: bad term arrays");
+  std::unique_ptr<mps_hamiltonian_dev> h(new mps_hamiltonian_dev());
+  h->n = n_qubits;
+  const uint64_t valid = n_qubits == 64 ? ~0ull : ((1ull << n_qubits) - 1ull);
+  struct T {
+    uint64_t x, z;
+    double c;
+  };
+  std::vector<T> terms;
+  for (int k = 0; k < hin->n_terms; ++k) {
+    uint64_t x = hin->x_mask[k], z = hin->z_mask[k];
+    double c = hin->coeff[k];
+    if (!std::isfinite(c)) return fail(MPS_EINVAL, "mps_hamiltonian_create: non-finite coefficient");
+    if ((x | z) & ~valid) return fail(MPS_EINVAL, "mps_hamiltonian_create: string acts beyond n_qubits");
+    if ((x | z) == 0) {
+      h->c0 += c;
+      continue;
+    }
+    terms.push_back({x, z, c});
+  }
+  std::sort(terms.begin(), terms.end(), [&](const T& A, const T& B) {
+    int a1 = first_site(A.x, A.z), a2 = first_site(B.x, B.z);
+    if (a1 != a2) return a1 < a2;
+    for (int s = a1; s < n_qubits; ++s) {
+      int u = sym(A.x, A.z, s), v = sym(B.x, B.z, s);
+      if (u != v) return u < v;
+    }
+    return false;
+  });
+  for (const auto& t : terms) {
+    h->x.push_back(t.x);
+    h->z.push_back(t.z);
+    h->c.push_back(t.c);
+  }
+  MPS_TRY(build_trie(h.get()));
+  MPS_TRY(h->d_coeff.alloc(std::max<size_t>(1, h->c.size()) * sizeof(double)));
+  if (!h->c.empty())
+    MPS_CU(cudaMemcpy(h->d_coeff.p, h->c.data(), h->c.size() * sizeof(double), cudaMemcpyHostToDevice));
+  *out = h.release();
+  return MPS_OK;
+}
+
+void mps_hamiltonian_free(mps_hamiltonian_dev* h) { delete h; }
+
+mps_status mps_apply_circuit_dev(mps_state* s, const mps_circuit* c, const double* theta, int32_t n_theta) {
+  clear_error();
+  if (!s) return fail(MPS_EINVAL, "mps_apply_circuit: state is NULL");
+  MPS_TRY(check_circuit(s, c, n_theta));
+  const double* d_theta = nullptr;
+  MPS_TRY(stage_theta(s, theta, n_theta, &d_theta));
+  MPS_TRY(ensure_forward_scratch(s->L, *s->ws));
+  MPS_TRY(gate_matrices(s, c, d_theta, n_theta));
+  Ctx cx{&s->L, &s->cfg, s->st, s->status.as<int>(), s->ws.get()};
+  MPS_TRY(forward_gates(cx, s->buf, c, s->ws->G.as<double2>(), 0, c->n_gates, nullptr));
+  return check_status_word(s->st, s->status, "mps_apply_circuit");
+}
+
+mps_status mps_apply_circuit(mps_state* s, const mps_gate* gates, int32_t n_gates, const double* theta,
+                             int32_t n_theta) {
+  clear_error();
+  if (!s) return fail(MPS_EINVAL, "mps_apply_circuit: state is NULL");
+  mps_circuit* c = nullptr;
+  MPS_TRY(mps_circuit_create(s->L.n, gates, n_gates, &c));
+  std::unique_ptr<mps_circuit> hold(c);
+  return mps_apply_circuit_dev(s, c, theta, n_theta);
+}
+
+mps_status mps_energy_dev(const mps_state* s, const mps_hamiltonian_dev* h, double* E_out, double* expect_out) {
+  clear_error();
+  if (!s || !h || !E_out) return fail(MPS_EINVAL, "mps_energy: NULL argument");
+  if (h->n != s->L.n) return fail(MPS_EINVAL, "mps_energy: Hamiltonian and state have different qubit counts");
+  mps_state* ms = const_cast<mps_state*>(s);
+  Workspace& w = *ms->ws;
+  const int nt = (int)h->x.size();
+  MPS_TRY(w.scalars.ensure((2 + std::max(1, nt)) * sizeof(double)));
+  double* dE = w.scalars.as<double>();
+  double* dX = expect_out ? dE + 2 : nullptr;
+  MPS_TRY(energy_pass_impl(s->L, s->buf, s->st, ms->status.as<int>(), const_cast<mps_hamiltonian_dev*>(h), dE, dX,
+                           nullptr));
+  MPS_TRY(put_out(E_out, dE, 1, s->st));
+  MPS_TRY(put_out(expect_out, dX, nt, s->st));
+  return check_status_word(s->st, ms->status, "mps_energy");
+}
+
+mps_status mps_energy(const mps_state* s, const mps_hamiltonian* h, double* E_out) {
+  clear_error();
+  if (!s || !h) return fail(MPS_EINVAL, "mps_energy: NULL argument");
+  mps_hamiltonian_dev* hd = nullptr;
+  MPS_TRY(mps_hamiltonian_create(s->L.n, h, &hd));
+  std::unique_ptr<mps_hamiltonian_dev> hold(hd);
+  return mps_energy_dev(s, hd, E_out, nullptr);
+}
+
+mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const double* theta, int32_t n_theta,
+                               const mps_hamiltonian_dev* hc, double* E_out, double* grad_out,
+                               double* gate_grad_out) {
+  clear_error();
+  if (!s0 || !hc || !E_out || (n_theta > 0 && !grad_out)) return fail(MPS_EINVAL, "mps_energy_grad: NULL argument");
+  mps_state* s = const_cast<mps_state*>(s0);
+  mps_hamiltonian_dev* h = const_cast<mps_hamiltonian_dev*>(hc);
+  if (h->n != s->L.n) return fail(MPS_EINVAL, "mps_energy_grad: Hamiltonian and state have different qubit counts");
+  MPS_TRY(check_circuit(s, c, n_theta));
+  const Layout& L = s->L;
+  Workspace& w = *s->ws;
+  const double* d_theta = nullptr;
+  MPS_TRY(stage_theta(s, theta, n_theta, &d_theta));
+  MPS_TRY(ensure_forward_scratch(L, w));
+  MPS_TRY(gate_matrices(s, c, d_theta, n_theta));
+  const int ng = c->n_gates;
+  const int K = std::max(1, s->cfg.checkpoint_every);
+  const int nseg = (ng + K - 1) / K;
+  if (!w.work_ok) {
+    MPS_TRY(w.work.alloc(L));
+    MPS_TRY(w.rec.alloc(L));
+    w.work_ok = true;
+  }
+  while ((int)w.snaps.size() < nseg) {
+    w.snaps.emplace_back(new StateBuf());
+    MPS_TRY(w.snaps.back()->alloc(L));
+  }
+  // tape arena for the largest segment
+  auto slot_elems = [&](int b, size_t* cplx, size_t* dbl) {
+    const size_t Dl = L.cap[b], Dm = L.cap[b + 1], Dr = L.cap[b + 2], m = 2 * Dl, nc = 2 * Dr;
+    *cplx = Dl * 2 * Dm + Dm * 2 * Dr + 2 * m * nc + nc * nc;
+    *dbl = nc + Dl + 2;   // s, lambda_left, dims (4 ints)
+  };
+  size_t arena = 0;
+  for (int seg = 0; seg < nseg; ++seg) {
+    size_t tot = 0;
+    for (int t = seg * K; t < std::min(ng, (seg + 1) * K); ++t) {
+      size_t cp, db;
+      slot_elems(c->host[t].bond, &cp, &db);
+      tot += align256(cp * sizeof(double2)) + align256(db * sizeof(double));
+    }
+    arena = std::max(arena, tot);
+  }
+  MPS_TRY(w.tape.ensure(std::max<size_t>(arena, 256)));
+  const size_t mc = 2 * (size_t)L.max_cap, nc = 2 * (size_t)L.max_cap, kc = L.max_cap;
+  const size_t rv_elems[] = {nc * kc, mc * nc, nc * kc, nc * nc, mc * nc, mc * nc, mc * nc, mc * nc, 16};
+  size_t rv_total = 0;
+  for (size_t e : rv_elems) rv_total += align256(e * sizeof(double2));
+  rv_total += align256(nc * sizeof(double));
+  MPS_TRY(w.rv.ensure(rv_total));
+  {
+    char* p = w.rv.as<char>();
+    double2** dst[] = {&w.Vbar, &w.Cbar, &w.Y, &w.Km, &w.T1, &w.Ctbar, &w.Theta, &w.Thbar, &w.Gbar};
+    for (int i = 0; i < 9; ++i) {
+      *dst[i] = reinterpret_cast<double2*>(p);
+      p += align256(rv_elems[i] * sizeof(double2));
+    }
+    w.wbar = reinterpret_cast<double*>(p);
+  }
+  MPS_TRY(w.Bbar.ensure(L.site_elems() * sizeof(double2)));
+  MPS_TRY(w.lambar.ensure(L.lam_elems() * sizeof(double)));
+  MPS_TRY(w.gate_grad.ensure(std::max(1, ng) * sizeof(double)));
+  MPS_TRY(w.grad.ensure(std::max(1, n_theta) * sizeof(double)));
+  MPS_TRY(w.scalars.ensure(4 * sizeof(double)));
+  Ctx cx{&L, &s->cfg, s->st, s->status.as<int>(), &w};
+  const double2* G = w.G.as<double2>();
+  const double2* dG = w.dG.as<double2>();
+  // forward with snapshots
+  MPS_TRY(w.work.copy_from(s->buf, L, s->st));
+  for (int seg = 0; seg < nseg; ++seg) {
+    MPS_TRY(w.snaps[seg]->copy_from(w.work, L, s->st));
+    MPS_TRY(forward_gates(cx, w.work, c, G, seg * K, std::min(ng, (seg + 1) * K), nullptr));
+  }
+  // energy and its cotangent
+  double* dE = w.scalars.as<double>();
+  MPS_TRY(energy_pass_impl(L, w.work, s->st, s->status.as<int>(), h, dE, nullptr, w.Bbar.as<double2>()));
+  MPS_CU(cudaMemsetAsync(w.lambar.p, 0, L.lam_elems() * sizeof(double), s->st));
+  MPS_CU(cudaMemsetAsync(w.gate_grad.p, 0, std::max(1, ng) * sizeof(double), s->st));
+  // reverse, segment by segment
+  std::vector<TapeSlot> tapes;
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int g0 = seg * K, g1 = std::min(ng, (seg + 1) * K);
+    tapes.assign(g1 - g0, TapeSlot{});
+    char* p = w.tape.as<char>();
+    for (int t = g0; t < g1; ++t) {
+      const int b = c->host[t].bond;
+      const size_t Dl = L.cap[b], Dm = L.cap[b + 1], Dr = L.cap[b + 2], m = 2 * Dl, ncol = 2 * Dr;
+      size_t cp, db;
+      slot_elems(b, &cp, &db);
+      TapeSlot& tp = tapes[t - g0];
+      double2* z = reinterpret_cast<double2*>(p);
+      tp.Bl = z;
+      tp.Br = tp.Bl + Dl * 2 * Dm;
+      tp.C = tp.Br + Dm * 2 * Dr;
+      tp.W = tp.C + m * ncol;
+      tp.Vs = tp.W + m * ncol;
+      p += align256(cp * sizeof(double2));
+      double* dd = reinterpret_cast<double*>(p);
+      tp.s = dd;
+      tp.lamL = dd + ncol;
+      tp.dims = reinterpret_cast<int*>(dd + ncol + Dl);
+      p += align256(db * sizeof(double));
+    }
+    MPS_TRY(w.rec.copy_from(*w.snaps[seg], L, s->st));
+    MPS_TRY(forward_gates(cx, w.rec, c, G, g0, g1, &tapes));
+    for (int t = g1 - 1; t >= g0; --t)
+      MPS_TRY(reverse_gate(cx, t, c->host[t].bond, tapes[t - g0], w.Bbar.as<double2>(), w.lambar.as<double>(), G, dG,
+                           w.gate_grad.as<double>()));
+    MPS_CU(cudaGetLastError());
+  }
+  const int nth_c = c->max_theta_idx + 1;
+  if (n_theta > 0) {
+    MPS_CU(cudaMemsetAsync(w.grad.p, 0, n_theta * sizeof(double), s->st));
+    launch_theta_reduce(w.gate_grad.as<double>(), c->csr_off.as<int>(), c->csr_gate.as<int>(),
+                        c->csr_scale.as<double>(), nth_c, w.grad.as<double>(), s->st);
+  }
+  MPS_TRY(put_out(E_out, dE, 1, s->st));
+  MPS_TRY(put_out(grad_out, w.grad.as<double>(), n_theta, s->st));
+  MPS_TRY(put_out(gate_grad_out, w.gate_grad.as<double>(), ng, s->st));
+  return check_status_word(s->st, s->status, "mps_energy_grad");
+}
+
+mps_status mps_energy_grad(const mps_state* s0, const mps_gate* gates, int32_t n_gates, const double* theta,
+                           int32_t n_theta, const mps_hamiltonian* h, double* E_out, double* grad_out,
+                           double* gate_grad_out) {
+  clear_error();
+  if (!s0 || !h) return fail(MPS_EINVAL, "mps_energy_grad: NULL argument");
+  mps_circuit* c = nullptr;
+  MPS_TRY(mps_circuit_create(s0->L.n, gates, n_gates, &c));
+  std::unique_ptr<mps_circuit> hold_c(c);
+  mps_hamiltonian_dev* hd = nullptr;
+  MPS_TRY(mps_hamiltonian_create(s0->L.n, h, &hd));
+  std::unique_ptr<mps_hamiltonian_dev> hold_h(hd);
+  return mps_energy_grad_dev(s0, c, theta, n_theta, hd, E_out, grad_out, gate_grad_out);
+}
+
+}  // extern "C"

@@ -1,0 +1,179 @@
+"""GPU (C ABI) against the CPU oracle on the same seeded inputs.
+
+Tolerances (FP64 path): relative 1e-10 on E, 1e-9 on ||g||; Schmidt values 1e-10.
+"""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import ansatz, mps as OM, pauli, statevector as SV
+
+pytestmark = pytest.mark.gpu
+
+E_TOL, G_TOL = 1e-10, 1e-9
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2211_07983_gb300 import build
+    build.build()
+    import paper_2211_07983_gb300 as M
+    return M
+
+
+def prepare(M, p, excs=None, D=None, eps=None, K=0):
+    excs = p.excitations if excs is None else excs
+    D = p.spec.D if D is None else D
+    eps = p.spec.eps if eps is None else eps
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    gates = M.compile_excitations(p.n, excs)
+    st = M.State.product(p.bits, D, eps, checkpoint_every=K)
+    return st, M.Circuit(p.n, gates), M.Hamiltonian(p.n, x, z, c), p.theta[: len(excs)]
+
+
+def oracle(p, excs=None, D=None, eps=None, K=512):
+    excs = p.excitations if excs is None else excs
+    D = p.spec.D if D is None else D
+    eps = p.spec.eps if eps is None else eps
+    oh = pauli.jw_hamiltonian(p.h, p.eri)
+    og = ansatz.compile_circuit(p.n, excs)
+    return OM.energy_grad(OM.init_product(p.bits), og, p.theta[: len(excs)], oh, D, eps, checkpoint_every=K), og, oh
+
+
+def small(n=8, n_e=4, D=64, eps=1e-12, cfg=90):
+    return S.make_problem(cfg, spec=S.ConfigSpec(f"n{n}_D{D}", n=n, n_e=n_e, D=D, eps=eps, decay=2.0))
+
+
+def test_product_state_roundtrip(M):
+    st = M.State.product([1, 0, 1, 1], 8, 1e-12)
+    dims, lams, B = st.read()
+    assert list(dims) == [1] * 5
+    for s, b in enumerate([1, 0, 1, 1]):
+        want = np.zeros((1, 2, 1), dtype=complex)
+        want[0, b, 0] = 1
+        assert np.array_equal(B[s], want)
+
+
+@pytest.mark.parametrize("case", ["cfg0", "n8", "n8_trunc"])
+def test_forward_state_matches_oracle(M, case):
+    if case == "cfg0":
+        p, D, eps = S.make_problem(0), None, None
+    elif case == "n8":
+        p, D, eps = small(), None, None
+    else:
+        p, D, eps = small(D=4, eps=1e-10), 4, 1e-10
+    excs = p.excitations[:12] if case == "n8_trunc" else p.excitations
+    st, circ, ham, th = prepare(M, p, excs, D, eps)
+    M.apply_circuit(st, circ, th)
+    dims, lams, B = st.read()
+    og = ansatz.compile_circuit(p.n, excs)
+    ref = OM.apply_circuit(OM.init_product(p.bits), og, th, D or p.spec.D, eps or p.spec.eps)
+    assert list(dims[1:-1]) == ref.bond_dims()
+    for a, b in zip(lams, ref.lam):
+        assert np.abs(a - b).max() < 1e-10
+    gpu_state = OM.MPS(B, lams)
+    psi_gpu, psi_ref = OM.to_dense(gpu_state), OM.to_dense(ref)
+    assert np.abs(psi_gpu - psi_ref).max() < 1e-10          # the state is gauge independent
+    # exact right-canonical form only without truncation; otherwise the same defect as the oracle
+    assert abs(OM.right_canonical_residual(gpu_state) - OM.right_canonical_residual(ref)) < 1e-10
+
+
+@pytest.mark.parametrize("case", ["cfg0", "n8", "cfg1_prefix"])
+def test_energy_and_expectations(M, case):
+    if case == "cfg0":
+        p, excs = S.make_problem(0), None
+    elif case == "n8":
+        p, excs = small(), None
+    else:
+        p = S.make_problem(1)
+        excs = p.excitations[:30]
+    excs = p.excitations if excs is None else excs
+    st, circ, ham, th = prepare(M, p, excs)
+    M.apply_circuit(st, circ, th)
+    E, ex = M.energy(st, ham, expect=True)
+    og = ansatz.compile_circuit(p.n, excs)
+    ref = OM.apply_circuit(OM.init_product(p.bits), og, th, p.spec.D, p.spec.eps)
+    oh = pauli.jw_hamiltonian(p.h, p.eri)
+    Er = OM.energy(ref, oh)
+    assert abs(E - Er) <= E_TOL * max(1.0, abs(Er))
+    e, Z = OM.string_expectations(ref, oh)
+    nonid = [k for k, (x, z) in enumerate(zip(oh.x, oh.z)) if x | z]
+    assert np.abs(ex - e.real[nonid] / Z.real).max() < 1e-11
+
+
+@pytest.mark.parametrize("case", ["cfg0", "n8", "n8_trunc", "cfg1_prefix"])
+def test_energy_grad_matches_oracle(M, case):
+    K = 512
+    if case == "cfg0":
+        p, excs, D, eps = S.make_problem(0), None, None, None
+    elif case == "n8":
+        p, excs, D, eps = small(), None, None, None
+        K = 37
+    elif case == "n8_trunc":
+        p, D, eps = small(D=4, eps=1e-10), 4, 1e-10
+        excs = p.excitations[:12]
+        K = 5
+    else:
+        p = S.make_problem(1)
+        excs, D, eps = p.excitations[:20], None, None
+    st, circ, ham, th = prepare(M, p, excs, D, eps, K)
+    E, g, gg = M.energy_grad(st, circ, th, ham, gate_grad=True)
+    r, og, oh = oracle(p, excs, D, eps, K)
+    assert abs(E - r.E) <= E_TOL * max(1.0, abs(r.E))
+    assert np.linalg.norm(g - r.grad) <= G_TOL * max(1.0, np.linalg.norm(r.grad))
+    assert np.abs(gg - r.gate_grad).max() <= G_TOL * max(1.0, np.abs(r.gate_grad).max())
+    # the reverse pass leaves the input state untouched
+    dims, _, B = st.read()
+    assert list(dims) == [1] * (p.n + 1)
+
+
+def test_energy_grad_full_config1(M):
+    """n = 12, D = 64, all 117 excitations (7355 gates), 601 strings."""
+    p = S.make_problem(1)
+    st, circ, ham, th = prepare(M, p)
+    E, g = M.energy_grad(st, circ, th, ham)
+    r, _, _ = oracle(p)
+    assert abs(E - r.E) <= E_TOL * max(1.0, abs(r.E))
+    assert np.linalg.norm(g - r.grad) <= G_TOL * max(1.0, np.linalg.norm(r.grad))
+
+
+def test_statevector_pin_through_gpu(M):
+    """No truncation: the GPU gradient equals Algorithm 1 on a dense state vector."""
+    p = small()
+    st, circ, ham, th = prepare(M, p)
+    E, g = M.energy_grad(st, circ, th, ham)
+    og = ansatz.compile_circuit(p.n, p.excitations)
+    Es, gs, _ = SV.gradient(p.bits, og, th, pauli.jw_hamiltonian(p.h, p.eri))
+    assert abs(E - Es) < 1e-10
+    assert np.linalg.norm(g - gs) < 1e-9 * max(1.0, np.linalg.norm(gs))
+
+
+def test_device_resident_inputs_and_outputs(M):
+    import torch
+    p = S.make_problem(0)
+    st, circ, ham, th = prepare(M, p)
+    E_h, g_h = M.energy_grad(st, circ, th, ham)
+    th_d = torch.tensor(th, device="cuda")
+    E_d = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g_d = torch.zeros(len(th), dtype=torch.float64, device="cuda")
+    M.energy_grad(st, circ, th_d, ham, out=(E_d, g_d))
+    assert E_d.item() == E_h
+    assert np.array_equal(g_d.cpu().numpy(), g_h)       # same kernels, same order: bit-identical
+
+
+def test_invalid_arguments_are_reported(M):
+    from paper_2211_07983_gb300._lib import MpsError
+    p = S.make_problem(0)
+    st, circ, ham, th = prepare(M, p)
+    with pytest.raises(MpsError):
+        M.energy_grad(st, circ, th[:1], ham)                  # theta index out of range
+    bad = th.copy()
+    bad[0] = np.nan
+    with pytest.raises(MpsError):
+        M.energy_grad(st, circ, bad, ham)                     # non-finite angle
+    with pytest.raises(MpsError):
+        M.State.product([1, 0, 1, 0], 0, 1e-12)               # D < 1
+    E, g = M.energy_grad(st, circ, th, ham)                   # the handle still works
+    assert np.isfinite(E)
