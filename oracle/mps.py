@@ -22,8 +22,8 @@ Readings:
 * The gradient is the exact derivative of this truncated forward pass with the
   kept count k held fixed (the "local" approach of Sec. 4 made exact): the SVD is
   differentiated through M = C~^+ C~ = V diag(s^2) V^+ with the full spectrum,
-  F_ij = (w_j - w_i) / ((w_j - w_i)^2 + eta), eta = (1e-12 w_1)^2; singular values at
-  or below 1e-13 s_1 count as exact zeros there (see NULL_REL).
+  F_ij = 1/(w_j - w_i), set to 0 for pairs degenerate to within 1e-10 (DEGEN_REL);
+  singular values at or below 1e-13 s_1 count as exact zeros (NULL_REL).
 """
 from __future__ import annotations
 
@@ -34,7 +34,10 @@ import numpy as np
 
 from . import pauli
 
-ETA_REL = 1e-12
+# Pairs of squared singular values with |w_i - w_j| <= DEGEN_REL * max(w_i, w_j) count as
+# exactly degenerate: their F_ij is 0.  A rotation inside an exactly degenerate block leaves
+# E unchanged, and a singular-value split at rounding level must not be divided by.
+DEGEN_REL = 1e-10
 # Singular values at or below NULL_REL * s_1 are rounding noise of an exactly rank-deficient
 # matrix (particle-number and spin symmetry make many two-site tensors rank deficient); the
 # adjoint treats them as exact zeros: w_i = 0 and the column (C~ V)_i = 0.
@@ -235,10 +238,9 @@ def svd_adjoint(Cm, s, V, k, sbar_k, Vbar_k):
     wbar[:k] = sbar_k / (2.0 * s[:k])
     Vbar = np.zeros((ncol, ncol), dtype=complex)
     Vbar[:, :k] = Vbar_k
-    eta = (ETA_REL * w[0]) ** 2
     dw = w[None, :] - w[:, None]                  # dw[i, j] = w_j - w_i
-    F = dw / (dw * dw + eta)
-    np.fill_diagonal(F, 0.0)
+    big = np.abs(dw) > DEGEN_REL * np.maximum(w[None, :], w[:, None])
+    F = np.where(big, 1.0 / np.where(big, dw, 1.0), 0.0)   # diagonal: dw = 0 -> 0
     J = F * (V.conj().T @ Vbar)
     W = Cm @ V
     W[:, null] = 0.0
