@@ -171,6 +171,16 @@ mps_status mps_energy_dev(const mps_state* s, const mps_hamiltonian_dev* h, doub
                           double* expect_out);
 
 /*
+ * Energy cotangent (step S7): E and Bbar_s = dE/dB_s* of the state itself, i.e.
+ * [sum_k c_k env_k(s) - E env_I(s)] / <psi|psi> with env_P(s) the network of
+ * <psi|P|psi> with conj(B_s) removed (Sec. 4, Eq. expecgrad: dE/d<psi| = H|psi>
+ * normalised).  Bbar_out: host or device, complex values as interleaved doubles in the
+ * layout of mps_read_state's `tensors` (current bond dims).
+ */
+mps_status mps_energy_cotangent_dev(const mps_state* s, const mps_hamiltonian_dev* h, double* E_out,
+                                    double* Bbar_out);
+
+/*
  * E(theta) and dE/dtheta for |psi> = U(theta)|s0> (s0 is not modified): forward
  * pass with snapshots, energy, energy cotangent dE/dB* (Sec. 4, Eq. expecgrad),
  * then the exact reverse pass through every truncated gate (Eq. circuitevolvegrad,
@@ -184,6 +194,18 @@ mps_status mps_energy_grad(const mps_state* s0, const mps_gate* gates, int32_t n
 mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const double* theta,
                                int32_t n_theta, const mps_hamiltonian_dev* h, double* E_out,
                                double* grad_out, double* gate_grad_out);
+
+/*
+ * The gate SVD on its own (steps S3-S4, Sec. 3): one-sided Jacobi SVD in FP64 of a complex
+ * m x ncol matrix A (m, ncol even, <= 512), columns orthogonalised, V accumulated, sorted
+ * descending, then the truncation rule k = max(1, min(D, #{s_i/||s||_2 > eps})).
+ *   A: host or device, row-major, interleaved (re, im)
+ *   s_out: ncol doubles; V_out: ncol x ncol complex (row-major, V[r][j] = component r of
+ *   right singular vector j); W_out: m x ncol complex, W = A V (row-major); k_out: one int.
+ *   Outputs: host or device.  Uses the default stream and synchronises.
+ */
+mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, double eps, double* s_out,
+                       double* V_out, double* W_out, int32_t* k_out);
 
 /* Release a state (NULL-safe). */
 void mps_free(mps_state* s);

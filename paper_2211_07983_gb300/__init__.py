@@ -7,7 +7,7 @@ include/mps.h).  This package holds its ctypes binding (`api`), the autograd wra
 and fails loudly if the library was not built.
 """
 from .api import (Circuit, Hamiltonian, State, apply_circuit, build_hamiltonian, compile_excitations, energy,
-                  energy_grad, kernel_launches)
+                  energy_cotangent, energy_grad, kernel_launches, svd)
 
 __all__ = ["Circuit", "Hamiltonian", "State", "apply_circuit", "build_hamiltonian", "compile_excitations",
-           "energy", "energy_grad", "kernel_launches"]
+           "energy", "energy_cotangent", "energy_grad", "kernel_launches", "svd"]

@@ -65,10 +65,13 @@ _SIGS = {
     "mps_apply_circuit_dev": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),
     "mps_energy": (c_int32, [c_void_p, P(MpsHamiltonian), c_void_p]),
     "mps_energy_dev": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "mps_energy_cotangent_dev": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "mps_energy_grad": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_int32, P(MpsHamiltonian), c_void_p,
                                   c_void_p, c_void_p]),
     "mps_energy_grad_dev": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p,
                                       c_void_p]),
+    "mps_svd_dev": (c_int32, [c_int32, c_int32, c_void_p, c_int32, c_double, c_void_p, c_void_p, c_void_p,
+                              c_void_p]),
     "mps_free": (None, [c_void_p]),
     "mps_last_error": (ctypes.c_char_p, []),
     "mps_kernel_launches": (c_int64, []),

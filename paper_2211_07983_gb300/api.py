@@ -207,6 +207,22 @@ def energy(state: State, ham: Hamiltonian, expect=False):
     return (float(E[0]), ex) if expect else float(E[0])
 
 
+def energy_cotangent(state: State, ham: Hamiltonian):
+    """mps_energy_cotangent_dev: E and dE/dB_s* per site (list of [Dl, 2, Dr] arrays)."""
+    dims, _, _ = state.read()
+    ne = int(sum(dims[s] * 2 * dims[s + 1] for s in range(state.n)))
+    E = np.zeros(1)
+    buf = np.zeros(2 * max(ne, 1))
+    check(_lib.load().mps_energy_cotangent_dev(state._h, ham._h, _ptr(E), _ptr(buf)))
+    cplx = buf[: 2 * ne].view(np.complex128)
+    out, o = [], 0
+    for s in range(state.n):
+        e = dims[s] * 2 * dims[s + 1]
+        out.append(cplx[o:o + e].reshape(dims[s], 2, dims[s + 1]).copy())
+        o += e
+    return float(E[0]), out
+
+
 def energy_grad(state0: State, circuit: Circuit, theta, ham: Hamiltonian, out=None, gate_grad=False):
     """mps_energy_grad_dev: E(theta), dE/dtheta (and dE/dphi per gate) of U(theta)|state0>.
 
@@ -223,6 +239,18 @@ def energy_grad(state0: State, circuit: Circuit, theta, ham: Hamiltonian, out=No
     if out is not None:
         return out
     return (float(E_out[0]), g_out, gg) if gate_grad else (float(E_out[0]), g_out)
+
+
+def svd(A: np.ndarray, D: int, eps: float):
+    """mps_svd_dev: the GPU gate SVD of one complex matrix -> (s, V, W = A V, k)."""
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    m, ncol = A.shape
+    s = np.zeros(ncol)
+    V = np.zeros((ncol, ncol), dtype=np.complex128)
+    W = np.zeros((m, ncol), dtype=np.complex128)
+    k = np.zeros(1, dtype=np.int32)
+    check(_lib.load().mps_svd_dev(m, ncol, _ptr(A), D, eps, _ptr(s), _ptr(V), _ptr(W), _ptr(k)))
+    return s, V, W, int(k[0])
 
 
 def kernel_launches() -> int:

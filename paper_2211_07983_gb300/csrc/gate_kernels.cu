@@ -93,6 +93,7 @@ __global__ void contract_kernel(const double2* __restrict__ Bl, const double2* _
 constexpr int SVD_THREADS = 256;
 constexpr int SVD_MAX_SWEEPS = 60;
 constexpr double SVD_NULL_REL = 1e-13;   // numerical-zero singular values (relative to s_max)
+constexpr double SVD_DEGEN_REL = 1e-10;  // exactly degenerate pairs of squared singular values
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -312,21 +313,16 @@ __global__ void build_K_kernel(const double2* __restrict__ Y, const double* __re
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ncol * ncol) return;
   const int i = t / ncol, j = t % ncol;
-  const double w0 = s[0] * s[0];
-  const double eta = (1e-12 * w0) * (1e-12 * w0);
   // numerical zeros (s <= SVD_NULL_REL s_1) enter as exact zeros
   const double wi = s[i] > SVD_NULL_REL * s[0] ? s[i] * s[i] : 0.0;
   const double wj = s[j] > SVD_NULL_REL * s[0] ? s[j] * s[j] : 0.0;
+  // F_ij = 1/(w_j - w_i), 0 inside exactly degenerate pairs (|dw| <= SVD_DEGEN_REL max(w))
+  const double dw = wj - wi;
+  const double F = fabs(dw) > SVD_DEGEN_REL * fmax(wi, wj) ? 1.0 / dw : 0.0;
   double2 v = make_double2(i == j ? wbar[i] : 0.0, 0.0);
   if (i != j) {
-    if (j < k) {  // J_ij = F_ij Y_ij, F_ij = (w_j - w_i) / ((w_j - w_i)^2 + eta)
-      const double dw = wj - wi;
-      v = cadd(v, cscale(Y[(size_t)i * k + j], dw / (dw * dw + eta)));
-    }
-    if (i < k) {  // (J^H)_ij = conj(F_ji Y_ji)
-      const double dw = wi - wj;
-      v = cadd(v, cscale(conjd(Y[(size_t)j * k + i]), dw / (dw * dw + eta)));
-    }
+    if (j < k) v = cadd(v, cscale(Y[(size_t)i * k + j], F));               // J_ij = F_ij Y_ij
+    if (i < k) v = cadd(v, cscale(conjd(Y[(size_t)j * k + i]), -F));       // (J^H)_ij = conj(F_ji Y_ji)
   }
   Km[(size_t)i * ncol + j] = v;
 }

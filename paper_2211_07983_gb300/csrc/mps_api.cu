@@ -1077,6 +1077,121 @@ mps_status mps_energy_dev(const mps_state* s, const mps_hamiltonian_dev* h, doub
   return check_status_word(s->st, ms->status, "mps_energy");
 }
 
+mps_status mps_energy_cotangent_dev(const mps_state* s, const mps_hamiltonian_dev* h, double* E_out,
+                                    double* Bbar_out) {
+  clear_error();
+  if (!s || !h || !E_out || !Bbar_out) return fail(MPS_EINVAL, "mps_energy_cotangent: NULL argument");
+  if (h->n != s->L.n) return fail(MPS_EINVAL, "mps_energy_cotangent: qubit counts differ");
+  mps_state* ms = const_cast<mps_state*>(s);
+  Workspace& w = *ms->ws;
+  const Layout& L = s->L;
+  MPS_TRY(w.scalars.ensure(4 * sizeof(double)));
+  MPS_TRY(w.Bbar.ensure(L.site_elems() * sizeof(double2)));
+  double* dE = w.scalars.as<double>();
+  MPS_TRY(energy_pass_impl(L, s->buf, s->st, ms->status.as<int>(), const_cast<mps_hamiltonian_dev*>(h), dE, nullptr,
+                           w.Bbar.as<double2>()));
+  MPS_TRY(check_status_word(s->st, ms->status, "mps_energy_cotangent"));
+  std::vector<int> d(L.n + 1);
+  MPS_CU(cudaMemcpy(d.data(), s->buf.dims, (L.n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+  const bool dev = is_device_ptr(Bbar_out);
+  size_t o = 0;
+  for (int q = 0; q < L.n; ++q) {
+    size_t e = (size_t)d[q] * 2 * d[q + 1];
+    MPS_CU(cudaMemcpyAsync(Bbar_out + 2 * o, w.Bbar.as<double2>() + L.site_off[q], e * sizeof(double2),
+                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->st));
+    o += e;
+  }
+  MPS_TRY(put_out(E_out, dE, 1, s->st));
+  MPS_CU(cudaStreamSynchronize(s->st));
+  return MPS_OK;
+}
+
+mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, double eps, double* s_out,
+                       double* V_out, double* W_out, int32_t* k_out) {
+  clear_error();
+  if (!A || !s_out || !V_out || !W_out || !k_out) return fail(MPS_EINVAL, "mps_svd: NULL argument");
+  if (m < 2 || ncol < 2 || (m & 1) || (ncol & 1) || m > 512 || ncol > 512)
+    return fail(MPS_EINVAL, "mps_svd: m and ncol must be even and in 2..512");
+  if (D < 1 || !(eps >= 0.0)) return fail(MPS_EINVAL, "mps_svd: bad D or eps");
+  const size_t mn = (size_t)m * ncol, nn = (size_t)ncol * ncol;
+  DevBuf buf, status;
+  const size_t bytes = align256(mn * 16) * 3 + align256(nn * 16) * 2 + align256(ncol * 8) * 2 + 256 + 256;
+  MPS_TRY(buf.alloc(bytes));
+  MPS_TRY(status.alloc(sizeof(int)));
+  char* p = buf.as<char>();
+  auto take = [&](size_t b) {
+    char* q = p;
+    p += align256(b);
+    return q;
+  };
+  double2* Ain = reinterpret_cast<double2*>(take(mn * 16));
+  double2* Acm = reinterpret_cast<double2*>(take(mn * 16));
+  double2* W = reinterpret_cast<double2*>(take(mn * 16));
+  double2* Vw = reinterpret_cast<double2*>(take(nn * 16));
+  double2* Vs = reinterpret_cast<double2*>(take(nn * 16));
+  double* s = reinterpret_cast<double*>(take(ncol * 8));
+  double* lam = reinterpret_cast<double*>(take(ncol * 8));
+  int* dims = reinterpret_cast<int*>(take(256));
+  double* one = reinterpret_cast<double*>(take(256));
+  const bool dev_in = is_device_ptr(A);
+  MPS_CU(cudaMemcpy(Ain, A, mn * 16, dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+  int hd[3] = {m / 2, 1, ncol / 2};
+  MPS_CU(cudaMemcpy(dims, hd, sizeof(hd), cudaMemcpyHostToDevice));
+  std::vector<double> ones(m / 2, 1.0);
+  MPS_CU(cudaMemcpy(one, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice));
+  // row-major -> column-major working copy: GEMM with the identity would do, a transpose is enough
+  GemmBatch g{};
+  g.count = 1;
+  std::vector<double2> eye(nn, make_double2(0, 0));
+  for (int i = 0; i < ncol; ++i) eye[(size_t)i * ncol + i] = make_double2(1, 0);
+  MPS_CU(cudaMemcpy(Vs, eye.data(), nn * 16, cudaMemcpyHostToDevice));
+  // Acm (ncol x m row-major) = I (ncol x ncol) * Ain^T  -> column-major A
+  g.d[0] = make_desc(dims, Vs, OP_N, Ain, OP_T, Acm, dconst(ncol), dconst(m), dconst(ncol), dconst(ncol), dconst(ncol),
+                     dconst(m));
+  launch_zgemm_small(g, ncol, m, 0);
+  SvdArgs a{};
+  a.A = Acm;
+  a.Vw = Vw;
+  a.dims = dims;
+  a.b = 0;
+  a.D = D;
+  a.eps = eps;
+  a.Vs = Vs;
+  a.s = s;
+  a.lam_out = lam;
+  a.W = W;
+  a.tape_dims = nullptr;
+  a.lam_left = one;
+  a.lam_left_copy = nullptr;
+  a.status = status.as<int>();
+  launch_svd(a, 0);
+  MPS_CU(cudaGetLastError());
+  MPS_CU(cudaDeviceSynchronize());
+  int code = 0, k = 0;
+  MPS_CU(cudaMemcpy(&code, status.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (code) return fail((mps_status)code, "mps_svd: device status");
+  MPS_CU(cudaMemcpy(&k, dims + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  // Vs, W are column-major (column j contiguous); return them row-major
+  std::vector<double2> hV(nn), hW(mn), tV(nn), tW(mn);
+  MPS_CU(cudaMemcpy(hV.data(), Vs, nn * 16, cudaMemcpyDeviceToHost));
+  MPS_CU(cudaMemcpy(hW.data(), W, mn * 16, cudaMemcpyDeviceToHost));
+  for (int j = 0; j < ncol; ++j) {
+    for (int r = 0; r < ncol; ++r) tV[(size_t)r * ncol + j] = hV[(size_t)j * ncol + r];
+    for (int r = 0; r < m; ++r) tW[(size_t)r * ncol + j] = hW[(size_t)j * m + r];
+  }
+  auto out = [&](void* dst, const void* src, size_t b) -> mps_status {
+    MPS_CU(cudaMemcpy(dst, src, b, is_device_ptr(dst) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    return MPS_OK;
+  };
+  std::vector<double> hs(ncol);
+  MPS_CU(cudaMemcpy(hs.data(), s, ncol * 8, cudaMemcpyDeviceToHost));
+  MPS_TRY(out(s_out, hs.data(), ncol * 8));
+  MPS_TRY(out(V_out, tV.data(), nn * 16));
+  MPS_TRY(out(W_out, tW.data(), mn * 16));
+  MPS_TRY(out(k_out, &k, sizeof(int)));
+  return MPS_OK;
+}
+
 mps_status mps_energy(const mps_state* s, const mps_hamiltonian* h, double* E_out) {
   clear_error();
   if (!s || !h) return fail(MPS_EINVAL, "mps_energy: NULL argument");
