@@ -71,10 +71,15 @@ def init_product(bits) -> MPS:
 
 
 def truncation_rank(s: np.ndarray, D: int, eps: float) -> int:
+    """k = max(1, min(D, #{i : s_i/||s||_2 > eps and s_i > NULL_REL s_1})).
+
+    Values at rounding level (s_i <= NULL_REL s_1) are numerical zeros and are never kept,
+    whatever eps is (only matters for eps < 1e-13).
+    """
     norm = math.sqrt(float(np.sum(s * s)))
     if norm == 0.0:
         return 1
-    count = int(np.sum(s / norm > eps))
+    count = int(np.sum((s / norm > eps) & (s > NULL_REL * s[0])))
     return max(1, min(D, count))
 
 
