@@ -48,7 +48,8 @@ enum { MPS_PRECISION_FP64 = 0, MPS_PRECISION_MIXED = 1 };
 /* Simulation settings (Sec. 3 truncation rule; Sec. 4 checkpointed reverse pass). */
 typedef struct {
   int32_t max_bond;          /* D: bond-dimension cap, >= 1 */
-  double cutoff;             /* eps: keep singular values with s_i/||s||_2 > eps */
+  double cutoff;             /* eps: keep singular values with s_i/||s||_2 > eps (values
+                                at or below 1e-13 s_1 are numerical zeros, never kept) */
   int32_t precision;         /* MPS_PRECISION_FP64 (only value accepted by this build) */
   int32_t checkpoint_every;  /* reverse pass: MPS snapshot every k gates; 0 = 512 */
   void* cuda_stream;         /* cudaStream_t, NULL = default stream */
@@ -196,12 +197,14 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
                                double* grad_out, double* gate_grad_out);
 
 /*
- * The gate SVD on its own (steps S3-S4, Sec. 3): one-sided Jacobi SVD in FP64 of a complex
- * m x ncol matrix A (m, ncol even, <= 512), columns orthogonalised, V accumulated, sorted
- * descending, then the truncation rule k = max(1, min(D, #{s_i/||s||_2 > eps})).
+ * The gate SVD on its own (steps S3-S4, Sec. 3): one-sided Jacobi SVD of a complex m x ncol
+ * matrix A (m, ncol even, <= 512) on its shorter side, FP32 preconditioning sweeps followed by
+ * FP64 re-orthonormalisation and FP64 sweeps (FP64-accurate result), sorted descending, then
+ * the truncation rule k = max(1, min(D, #{s_i/||s||_2 > eps, s_i > 1e-13 s_1})).  With K = min(m, ncol):
  *   A: host or device, row-major, interleaved (re, im)
- *   s_out: ncol doubles; V_out: ncol x ncol complex (row-major, V[r][j] = component r of
- *   right singular vector j); W_out: m x ncol complex, W = A V (row-major); k_out: one int.
+ *   s_out: K doubles; V_out: ncol x K complex (row-major, V[r][j] = component r of right
+ *   singular vector j; zero for numerically-zero s_j when m < ncol); W_out: m x K complex,
+ *   W = A V (row-major; zero columns for numerically-zero s_j); k_out: one int.
  *   Outputs: host or device.  Uses the default stream and synchronises.
  */
 mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, double eps, double* s_out,

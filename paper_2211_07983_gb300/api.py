@@ -245,9 +245,10 @@ def svd(A: np.ndarray, D: int, eps: float):
     """mps_svd_dev: the GPU gate SVD of one complex matrix -> (s, V, W = A V, k)."""
     A = np.ascontiguousarray(A, dtype=np.complex128)
     m, ncol = A.shape
-    s = np.zeros(ncol)
-    V = np.zeros((ncol, ncol), dtype=np.complex128)
-    W = np.zeros((m, ncol), dtype=np.complex128)
+    K = min(m, ncol)
+    s = np.zeros(K)
+    V = np.zeros((ncol, K), dtype=np.complex128)
+    W = np.zeros((m, K), dtype=np.complex128)
     k = np.zeros(1, dtype=np.int32)
     check(_lib.load().mps_svd_dev(m, ncol, _ptr(A), D, eps, _ptr(s), _ptr(V), _ptr(W), _ptr(k)))
     return s, V, W, int(k[0])

@@ -1,5 +1,6 @@
 // Gate application (Sec. 3, two-qubit gate with Hastings' canonical-form update) and the
 // custom pieces of its exact adjoint (Sec. 4 / App. A rules), FP64.
+#include <algorithm>
 #include <cmath>
 
 #include "../../include/mps.h"
@@ -89,8 +90,16 @@ __global__ void contract_kernel(const double2* __restrict__ Bl, const double2* _
   }
 }
 
-// ---- one-sided Jacobi SVD ------------------------------------------------------------------
-constexpr int SVD_THREADS = 256;
+// ---- one-sided Jacobi SVD (FP32 preconditioning sweeps + FP64 sweeps) ----------------------
+//
+// The two-site matrix C~ (m x n) is orthogonalised on its shorter side: for m >= n the n columns
+// of X0 = C~ are rotated (Q accumulates V), for m < n the m columns of X0 = C~^H (Q accumulates
+// U).  GB300 runs FP64 at 1/58 of its FP32 rate, so the sweeps first run in FP32 on a complex64
+// copy; the accumulated rotation is then re-orthonormalised in FP64 (modified Gram-Schmidt),
+// X = X0 Q is re-formed in FP64 from the untouched input, and FP64 sweeps finish to the FP64
+// convergence criterion.  The result is an FP64-accurate SVD whose FP64 work is a few sweeps.
+// X, Q live in shared memory when they fit (the launcher decides), else in global scratch.
+constexpr int SVD_THREADS = 512;
 constexpr int SVD_MAX_SWEEPS = 60;
 constexpr double SVD_NULL_REL = 1e-13;   // numerical-zero singular values (relative to s_max)
 constexpr double SVD_DEGEN_REL = 1e-10;  // exactly degenerate pairs of squared singular values
@@ -100,38 +109,40 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
-__global__ void __launch_bounds__(SVD_THREADS) svd_kernel(SvdArgs p) {
-  const int b = p.b;
-  const int Dl = p.dims[b], Dr = p.dims[b + 2];
-  const int m = 2 * Dl, K = 2 * Dr;            // A is m x K, orthogonalise its K columns
-  const int Kp = K + (K & 1);                  // even count for the round-robin schedule
-  double2* A = p.A;
-  double2* V = p.Vw;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = SVD_THREADS / 32;
-  __shared__ double red[SVD_THREADS / 32];
-  __shared__ int rotated;
-  __shared__ double s_sh[1024];
-  __shared__ double fro2_sh;
+template <class T>
+struct Cplx;
+template <>
+struct Cplx<double> {
+  using t = double2;
+  __device__ static double2 mk(double x, double y) { return make_double2(x, y); }
+  __device__ static double sum(double v) { return warp_sum(v); }
+};
+template <>
+struct Cplx<float> {
+  using t = float2;
+  __device__ static float2 mk(float x, float y) { return make_float2(x, y); }
+  __device__ static float sum(float v) { return warp_sumf(v); }
+};
 
-  for (int e = tid; e < K * K; e += SVD_THREADS) V[e] = make_double2((e / K) == (e % K) ? 1.0 : 0.0, 0.0);
-  // ||A||_F^2 (columns below 1e-15 ||A||_F are treated as numerically zero)
-  double f = 0.0;
-  for (int e = tid; e < m * K; e += SVD_THREADS) f += A[e].x * A[e].x + A[e].y * A[e].y;
-  f = warp_sum(f);
-  if (lane == 0) red[warp] = f;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < nwarp; ++w) t += red[w];
-    fro2_sh = t;
-  }
-  __syncthreads();
-  const double tiny = 1e-30 * fro2_sh;          // (1e-15 ||A||_F)^2
-  const double tol = 4.0 * 2.220446049250313e-16 * sqrt((double)m);
+// Cyclic (round-robin) sweeps over the K columns of X (R rows, column j at X + j*R) with the
+// rotations accumulated into Q (K x K, column j at Q + j*K).  One warp per column pair.
+// Returns the number of sweeps run; *converged = 1 if the last sweep rotated nothing.
+template <class T>
+__device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int R, int K, T tol, T tiny,
+                             int max_sweeps, int* flag_sh, int* converged) {
+  using C2 = typename Cplx<T>::t;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const int Kp = K + (K & 1);
   int sweep = 0;
-  for (; sweep < SVD_MAX_SWEEPS; ++sweep) {
-    if (tid == 0) rotated = 0;
+  *converged = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) *flag_sh = 0;
     __syncthreads();
     for (int r = 0; r < Kp - 1; ++r) {
       for (int t = warp; t < Kp / 2; t += nwarp) {
@@ -144,96 +155,188 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(SvdArgs p) {
           qc = (r - t + Kp - 1) % (Kp - 1);
         }
         if (pc >= K || qc >= K) continue;
-        double2* ap = A + (size_t)pc * m;
-        double2* aq = A + (size_t)qc * m;
-        double al = 0.0, be = 0.0, gr = 0.0, gi = 0.0;
-        for (int i = lane; i < m; i += 32) {
-          double2 x = ap[i], y = aq[i];
+        C2* ap = X + (size_t)pc * R;
+        C2* aq = X + (size_t)qc * R;
+        T al = 0, be = 0, gr = 0, gi = 0;
+        for (int i = lane; i < R; i += 32) {
+          const C2 x = ap[i], y = aq[i];
           al += x.x * x.x + x.y * x.y;
           be += y.x * y.x + y.y * y.y;
-          gr += x.x * y.x + x.y * y.y;   // conj(x) * y
+          gr += x.x * y.x + x.y * y.y;   // conj(x) y
           gi += x.x * y.y - x.y * y.x;
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        gr = warp_sum(gr);
-        gi = warp_sum(gi);
+        al = Cplx<T>::sum(al);
+        be = Cplx<T>::sum(be);
+        gr = Cplx<T>::sum(gr);
+        gi = Cplx<T>::sum(gi);
         if (al < tiny || be < tiny) continue;
-        const double g = hypot(gr, gi);
+        const T g = hypot(gr, gi);
         if (!(g > tol * sqrt(al) * sqrt(be))) continue;
-        const double zeta = (be - al) / (2.0 * g);
-        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
-        const double2 ph = make_double2(gr / g, gi / g);   // e^{i phi}
+        const T zeta = (be - al) / (T(2) * g);
+        const T tt = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+        const T c = T(1) / sqrt(T(1) + tt * tt), s = c * tt;
+        const T pr = gr / g, pim = gi / g;                        // e^{i phi}
         // a_p' = c a_p - s e^{-i phi} a_q ; a_q' = s e^{i phi} a_p + c a_q
-        const double2 sp = cscale(ph, s), sm = cscale(conjd(ph), s);
-        for (int i = lane; i < m; i += 32) {
-          double2 x = ap[i], y = aq[i];
-          ap[i] = csub(cscale(x, c), cmul(sm, y));
-          aq[i] = cadd(cmul(sp, x), cscale(y, c));
+        const T spr = s * pr, spi = s * pim;
+        for (int i = lane; i < R; i += 32) {
+          const C2 x = ap[i], y = aq[i];
+          ap[i] = Cplx<T>::mk(c * x.x - (spr * y.x + spi * y.y), c * x.y - (spr * y.y - spi * y.x));
+          aq[i] = Cplx<T>::mk(spr * x.x - spi * x.y + c * y.x, spr * x.y + spi * x.x + c * y.y);
         }
-        double2* vp = V + (size_t)pc * K;
-        double2* vq = V + (size_t)qc * K;
+        C2* vp = Q + (size_t)pc * K;
+        C2* vq = Q + (size_t)qc * K;
         for (int i = lane; i < K; i += 32) {
-          double2 x = vp[i], y = vq[i];
-          vp[i] = csub(cscale(x, c), cmul(sm, y));
-          vq[i] = cadd(cmul(sp, x), cscale(y, c));
+          const C2 x = vp[i], y = vq[i];
+          vp[i] = Cplx<T>::mk(c * x.x - (spr * y.x + spi * y.y), c * x.y - (spr * y.y - spi * y.x));
+          vq[i] = Cplx<T>::mk(spr * x.x - spi * x.y + c * y.x, spr * x.y + spi * x.x + c * y.y);
         }
-        if (lane == 0) rotated = 1;
+        if (lane == 0) *flag_sh = 1;
       }
       __syncthreads();
     }
-    if (!rotated) break;
+    const int rot = *flag_sh;
+    __syncthreads();
+    if (!rot) {
+      *converged = 1;
+      return sweep + 1;
+    }
+  }
+  return sweep;
+}
+
+__global__ void __launch_bounds__(SVD_THREADS) svd_kernel(SvdArgs p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[SVD_THREADS / 32];
+  __shared__ double s_sh[512];
+  __shared__ int flag_sh, conv_sh, k_sh;
+  __shared__ double fro2_sh, smax_sh, nk_sh;
+  const int b = p.b;
+  const int Dl = p.dims[b], Dr = p.dims[b + 2];
+  const int m = 2 * Dl, n = 2 * Dr;
+  const bool tall = m >= n;
+  const int R = tall ? m : n, K = tall ? n : m;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = SVD_THREADS / 32;
+  double2* base = p.scratch ? p.scratch : reinterpret_cast<double2*>(smem_raw);
+  double2* Q64 = base;                                      // K x K
+  double2* X64 = base + (size_t)K * K;                      // R x K
+  float2* X32 = reinterpret_cast<float2*>(X64);             // R x K  (inside the X64 region)
+  float2* Q32 = X32 + (size_t)R * K;                        // K x K  (inside the X64 region, K <= R)
+  const double2* A = p.A;                                   // C~ column-major (m x n)
+  auto x0 = [&](int r, int j) -> double2 {                  // element (r, j) of X0
+    return tall ? A[(size_t)j * m + r] : conjd(A[(size_t)r * m + j]);
+  };
+  // ---- FP32 preconditioning sweeps ----
+  double f = 0.0;
+  for (int e = tid; e < R * K; e += SVD_THREADS) {
+    const int j = e / R, r = e % R;
+    const double2 v = x0(r, j);
+    f += v.x * v.x + v.y * v.y;
+    X32[(size_t)j * R + r] = make_float2((float)v.x, (float)v.y);
+  }
+  for (int e = tid; e < K * K; e += SVD_THREADS) Q32[e] = make_float2((e / K) == (e % K) ? 1.f : 0.f, 0.f);
+  f = warp_sum(f);
+  if (lane == 0) red[warp] = f;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nwarp; ++w) t += red[w];
+    fro2_sh = t;
+  }
+  __syncthreads();
+  int conv = 0;
+  jacobi_sweeps<float>(X32, Q32, R, K, 4.f * 1.1920929e-7f * sqrtf((float)R), (float)(1e-30 * fro2_sh) + 1e-37f,
+                       30, &flag_sh, &conv);
+  // ---- Q64 = orthonormalised Q32 (modified Gram-Schmidt, FP64) ----
+  for (int e = tid; e < K * K; e += SVD_THREADS) Q64[e] = make_double2((double)Q32[e].x, (double)Q32[e].y);
+  __syncthreads();
+  for (int j = 0; j < K; ++j) {
+    double2* qj = Q64 + (size_t)j * K;
+    if (warp == 0) {
+      double v = 0.0;
+      for (int i = lane; i < K; i += 32) v += qj[i].x * qj[i].x + qj[i].y * qj[i].y;
+      v = warp_sum(v);
+      const double inv = 1.0 / sqrt(v);
+      for (int i = lane; i < K; i += 32) qj[i] = cscale(qj[i], inv);
+    }
+    __syncthreads();
+    for (int l = j + 1 + warp; l < K; l += nwarp) {
+      double2* ql = Q64 + (size_t)l * K;
+      double pr = 0.0, pim = 0.0;
+      for (int i = lane; i < K; i += 32) {   // qj^H ql
+        pr += qj[i].x * ql[i].x + qj[i].y * ql[i].y;
+        pim += qj[i].x * ql[i].y - qj[i].y * ql[i].x;
+      }
+      pr = warp_sum(pr);
+      pim = warp_sum(pim);
+      const double2 d = make_double2(pr, pim);
+      for (int i = lane; i < K; i += 32) ql[i] = csub(ql[i], cmul(d, qj[i]));
+    }
     __syncthreads();
   }
-  if (sweep >= SVD_MAX_SWEEPS && tid == 0) set_status(p.status, MPS_ENOCONV);
-  // column norms -> singular values
+  // ---- X64 = X0 Q64 (FP64, from the untouched input) ----
+  for (int e = tid; e < R * K; e += SVD_THREADS) {
+    const int j = e / R, r = e % R;
+    const double2* qj = Q64 + (size_t)j * K;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l = 0; l < K; ++l) acc = cfma(x0(r, l), qj[l], acc);
+    X64[(size_t)j * R + r] = acc;
+  }
+  __syncthreads();
+  // ---- FP64 sweeps ----
+  jacobi_sweeps<double>(X64, Q64, R, K, 4.0 * 2.220446049250313e-16 * sqrt((double)R), 1e-30 * fro2_sh,
+                        SVD_MAX_SWEEPS, &flag_sh, &conv_sh);
+  if (tid == 0 && !conv_sh) set_status(p.status, MPS_ENOCONV);
+  // ---- singular values, order, outputs ----
   for (int j = warp; j < K; j += nwarp) {
     double v = 0.0;
-    for (int i = lane; i < m; i += 32) {
-      double2 x = A[(size_t)j * m + i];
+    for (int i = lane; i < R; i += 32) {
+      const double2 x = X64[(size_t)j * R + i];
       v += x.x * x.x + x.y * x.y;
     }
     v = warp_sum(v);
     if (lane == 0) s_sh[j] = sqrt(v);
   }
   __syncthreads();
-  // stable descending rank, then scatter sorted columns; for the tape, columns of A V whose
-  // singular value is at most SVD_NULL_REL * s_max are rounding noise of an exactly
-  // rank-deficient matrix and are stored as exact zeros (the adjoint relies on it)
-  __shared__ double smax_sh;
   if (tid == 0) {
     double mx = 0.0;
     for (int j = 0; j < K; ++j) mx = fmax(mx, s_sh[j]);
     smax_sh = mx;
   }
   __syncthreads();
-  for (int j = tid; j < K; j += SVD_THREADS) {
+  // Outputs, sorted descending (stable in the column index):
+  //   s[0..K), Vs: K columns of length n (right singular vectors; zero for numerical zeros when
+  //   they come from the wide orientation), W: K columns of length m (W_j = C~ v_j; stored as exact
+  //   zeros for numerical zeros, s_j <= SVD_NULL_REL s_max).
+  for (int j = warp; j < K; j += nwarp) {
     const double sj = s_sh[j];
     int rank = 0;
     for (int i = 0; i < K; ++i) {
       const double si = s_sh[i];
       rank += (si > sj) || (si == sj && i < j);
     }
-    p.s[rank] = sj;
-    for (int i = 0; i < K; ++i) p.Vs[(size_t)rank * K + i] = V[(size_t)j * K + i];
-    if (p.W) {
-      const bool null_col = !(sj > SVD_NULL_REL * smax_sh);
-      for (int i = 0; i < m; ++i)
-        p.W[(size_t)rank * m + i] = null_col ? make_double2(0.0, 0.0) : A[(size_t)j * m + i];
+    const bool null_col = !(sj > SVD_NULL_REL * smax_sh);
+    if (lane == 0) p.s[rank] = sj;
+    double2* vs = p.Vs + (size_t)rank * n;
+    double2* w = p.W ? p.W + (size_t)rank * m : nullptr;
+    if (tall) {   // V = Q, W = X
+      for (int i = lane; i < n; i += 32) vs[i] = Q64[(size_t)j * K + i];
+      if (w)
+        for (int i = lane; i < m; i += 32) w[i] = null_col ? make_double2(0, 0) : X64[(size_t)j * R + i];
+    } else {      // X = V S, Q = U: v_j = X_j / s_j, W_j = U_j s_j
+      const double inv = null_col ? 0.0 : 1.0 / sj;
+      for (int i = lane; i < n; i += 32) vs[i] = cscale(X64[(size_t)j * R + i], inv);
+      if (w)
+        for (int i = lane; i < m; i += 32) w[i] = null_col ? make_double2(0, 0) : cscale(Q64[(size_t)j * K + i], sj);
     }
   }
   __syncthreads();
-  __threadfence_block();
-  __shared__ int k_sh;
-  __shared__ double nk_sh;
   if (tid == 0) {
     double n2 = 0.0;
     for (int j = 0; j < K; ++j) n2 += p.s[j] * p.s[j];
     const double nrm = sqrt(n2);
     int cnt = 0;
-    if (nrm > 0.0 && isfinite(nrm)) {
-      for (int j = 0; j < K; ++j) cnt += (p.s[j] / nrm > p.eps);
+    if (nrm > 0.0 && isfinite(nrm)) {   // numerical zeros (s <= SVD_NULL_REL s_max) are never kept
+      for (int j = 0; j < K; ++j) cnt += (p.s[j] / nrm > p.eps) && (p.s[j] > SVD_NULL_REL * smax_sh);
     } else {
       set_status(p.status, MPS_ENUMERIC);
     }
@@ -257,6 +360,7 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(SvdArgs p) {
       p.tape_dims[1] = p.dims[b + 1];
       p.tape_dims[2] = Dr;
       p.tape_dims[3] = k;
+      p.tape_dims[4] = K;
     }
     p.dims[b + 1] = k;
   }
@@ -282,7 +386,7 @@ __global__ void conjT_kernel(const double2* __restrict__ Bbr, const int* __restr
 
 __global__ void sbar_kernel(double* lambar, const double* __restrict__ s, const int* __restrict__ td,
                             double* wbar) {
-  const int k = td[3], ncol = 2 * td[2];
+  const int k = td[3], ncol = td[4];
   __shared__ double nrm_sh, dot_sh;
   if (threadIdx.x == 0) {
     double n2 = 0.0;
@@ -309,10 +413,10 @@ __global__ void sbar_kernel(double* lambar, const double* __restrict__ s, const 
 
 __global__ void build_K_kernel(const double2* __restrict__ Y, const double* __restrict__ s,
                                const double* __restrict__ wbar, const int* __restrict__ td, double2* Km) {
-  const int k = td[3], ncol = 2 * td[2];
+  const int k = td[3], K = td[4];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ncol * ncol) return;
-  const int i = t / ncol, j = t % ncol;
+  if (t >= K * K) return;
+  const int i = t / K, j = t % K;
   // numerical zeros (s <= SVD_NULL_REL s_1) enter as exact zeros
   const double wi = s[i] > SVD_NULL_REL * s[0] ? s[i] * s[i] : 0.0;
   const double wj = s[j] > SVD_NULL_REL * s[0] ? s[j] * s[j] : 0.0;
@@ -324,7 +428,16 @@ __global__ void build_K_kernel(const double2* __restrict__ Y, const double* __re
     if (j < k) v = cadd(v, cscale(Y[(size_t)i * k + j], F));               // J_ij = F_ij Y_ij
     if (i < k) v = cadd(v, cscale(conjd(Y[(size_t)j * k + i]), -F));       // (J^H)_ij = conj(F_ji Y_ji)
   }
-  Km[(size_t)i * ncol + j] = v;
+  Km[(size_t)i * K + j] = v;
+}
+
+// Z[r][j] /= w_j (j < k): the complement term (W_k diag(1/w_k)) Z^H of the SVD adjoint
+__global__ void zscale_kernel(double2* Z, const double* __restrict__ s, const int* __restrict__ td) {
+  const int k = td[3], n = 2 * td[2];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * k) return;
+  const int j = t % k;
+  Z[t] = cscale(Z[t], 1.0 / (s[j] * s[j]));
 }
 
 __global__ void lam_scale_kernel(double2* Cbar, const double2* __restrict__ Ctbar,
@@ -435,8 +548,44 @@ void launch_contract(const double2* Bl, const double2* Br, const int* dims, int 
   note_launch();
 }
 
-void launch_svd(const SvdArgs& a, cudaStream_t st) {
-  svd_kernel<<<1, SVD_THREADS, 0, st>>>(a);
+size_t svd_smem_bytes(int m_cap, int n_cap) {
+  const size_t R = std::max(m_cap, n_cap), K = std::min(m_cap, n_cap);
+  return (K * K + R * K) * sizeof(double2);
+}
+
+// Largest dynamic shared memory the SVD kernel may use: the device's opt-in limit per block minus
+// the kernel's static shared memory (queried once; 0 if the attribute cannot be raised).
+static size_t svd_dynamic_limit() {
+  static size_t limit = (size_t)-1;
+  if (limit != (size_t)-1) return limit;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaFuncAttributes fa{};
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, svd_kernel) != cudaSuccess) {
+    cudaGetLastError();
+    limit = 0;
+    return limit;
+  }
+  size_t want = (size_t)optin > fa.sharedSizeBytes + 1024 ? (size_t)optin - fa.sharedSizeBytes - 1024 : 0;
+  if (cudaFuncSetAttribute(svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want) != cudaSuccess) {
+    cudaGetLastError();
+    want = 48 * 1024 > fa.sharedSizeBytes ? 48 * 1024 - fa.sharedSizeBytes : 0;
+  }
+  limit = want;
+  return limit;
+}
+
+bool svd_fits_smem(int m_cap, int n_cap) { return svd_smem_bytes(m_cap, n_cap) <= svd_dynamic_limit(); }
+
+void launch_svd(const SvdArgs& a, int m_cap, int n_cap, cudaStream_t st) {
+  SvdArgs b = a;
+  size_t smem = 0;
+  if (svd_fits_smem(m_cap, n_cap)) {
+    b.scratch = nullptr;
+    smem = svd_smem_bytes(m_cap, n_cap);
+  }
+  svd_kernel<<<1, SVD_THREADS, smem, st>>>(b);
   note_launch();
 }
 
@@ -459,8 +608,13 @@ void launch_sbar(double* lambar_slot, const double* s, const int* td, double* wb
 }
 
 void launch_build_K(const double2* Y, const double* s, const double* wbar, const int* td, double2* K,
-                    int max_ncol, cudaStream_t st) {
-  build_K_kernel<<<cdiv((long long)max_ncol * max_ncol, 256), 256, 0, st>>>(Y, s, wbar, td, K);
+                    int max_K, cudaStream_t st) {
+  build_K_kernel<<<cdiv((long long)max_K * max_K, 256), 256, 0, st>>>(Y, s, wbar, td, K);
+  note_launch();
+}
+
+void launch_zscale(double2* Z, const double* s, const int* td, int max_n, int max_k, cudaStream_t st) {
+  zscale_kernel<<<cdiv((long long)max_n * max_k, 256), 256, 0, st>>>(Z, s, td);
   note_launch();
 }
 

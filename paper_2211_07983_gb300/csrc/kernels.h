@@ -34,13 +34,15 @@ void launch_contract(const double2* Bl, const double2* Br, const int* dims, int 
                      const double* lam_left, double2* C, double2* A, int max_dl, int max_dr,
                      cudaStream_t st);
 
-// One-sided Jacobi SVD of A (m x ncol, column-major) with V accumulated, sorted descending,
-// truncated (Sec. 3 rule).  Writes Vs (sorted V, column-major), s (ncol, zero padded),
-// lam_out (slot b+1), dims[b+1] = k, and when non-null: W (sorted A V), tape_dims
-// {Dl, Dm, Dr, k} and lam_left_copy (slot b copied).
+// Gate SVD (steps S3-S4): A = lambda-scaled C~ (m x n, column-major).  FP32 preconditioning
+// sweeps, FP64 re-orthonormalisation, FP64 sweeps; orthogonalises K = min(m, n) columns.
+// Writes s (K values, descending), Vs (K right singular vectors of length n, column j at
+// Vs + j*n), lam_out (slot b+1), dims[b+1] = k, and when non-null: W (K columns of length m,
+// W_j = C~ v_j, zero for numerical zeros), tape_dims {Dl, Dm, Dr, k, K}, lam_left_copy.
+// scratch: global buffer of (K^2 + R K) complex values used when shared memory is too small.
 struct SvdArgs {
-  double2* A;
-  double2* Vw;
+  const double2* A;
+  double2* scratch;
   int* dims;
   int b;
   int D;
@@ -54,19 +56,22 @@ struct SvdArgs {
   double* lam_left_copy;
   int* status;
 };
-void launch_svd(const SvdArgs& a, cudaStream_t st);
+size_t svd_smem_bytes(int m_cap, int n_cap);
+bool svd_fits_smem(int m_cap, int n_cap);
+void launch_svd(const SvdArgs& a, int m_cap, int n_cap, cudaStream_t st);
 
 // B_{b+1} <- (Vs[:, :k])^H reshaped [k][2][Dr]
 void launch_vh_rows(const double2* Vs, const int* dims, int b, double2* Br_out, int max_k, int max_ncol,
                     cudaStream_t st);
 
-// ---- gate adjoint pieces; `td` = tape dims {Dl, Dm, Dr, k} ------------------------------------
+// ---- gate adjoint pieces; `td` = tape dims {Dl, Dm, Dr, k, K} ------------------------------------
 void launch_conjT(const double2* Bbar_r, const int* td, double2* Vbar, int max_k, int max_ncol,
                   cudaStream_t st);
 void launch_sbar(double* lambar_slot, const double* s, const int* td, double* wbar, int max_ncol,
                  cudaStream_t st);
 void launch_build_K(const double2* Y, const double* s, const double* wbar, const int* td, double2* K,
-                    int max_ncol, cudaStream_t st);
+                    int max_K, cudaStream_t st);
+void launch_zscale(double2* Z, const double* s, const int* td, int max_n, int max_k, cudaStream_t st);
 void launch_lam_scale(double2* Cbar, const double2* Ctbar, const double2* C, const double* lam_left,
                       const int* td, double* lambar_left, int max_dl, cudaStream_t st);
 void launch_gbar(const double2* Cbar, const double2* Theta, const int* td, const double2* dG,

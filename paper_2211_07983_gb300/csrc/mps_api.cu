@@ -114,7 +114,7 @@ struct TapeSlot {
 };
 
 struct Workspace {
-  DevBuf A, Vw, C, Vs, s;                         // forward scratch at the largest bond
+  DevBuf A, svd, C, Vs, s;                        // forward scratch at the largest bond
   DevBuf G, dG, theta, scalars, gate_grad, grad;  // per call
   StateBuf work, rec;                             // energy_grad working states
   std::vector<std::unique_ptr<StateBuf>> snaps;
@@ -138,7 +138,7 @@ struct Ctx {
 static mps_status ensure_forward_scratch(const Layout& L, Workspace& w) {
   const size_t mc = 2 * (size_t)L.max_cap, nc = 2 * (size_t)L.max_cap;
   MPS_TRY(w.A.ensure(mc * nc * sizeof(double2)));
-  MPS_TRY(w.Vw.ensure(nc * nc * sizeof(double2)));
+  MPS_TRY(w.svd.ensure(2 * nc * nc * sizeof(double2)));   // SVD scratch if shared memory is too small
   MPS_TRY(w.C.ensure(mc * nc * sizeof(double2)));
   MPS_TRY(w.Vs.ensure(nc * nc * sizeof(double2)));
   MPS_TRY(w.s.ensure(nc * sizeof(double)));
@@ -147,7 +147,7 @@ static mps_status ensure_forward_scratch(const Layout& L, Workspace& w) {
 
 static GemmDesc make_desc(const int* dims, const double2* A, int opA, const double2* B, int opB, double2* C,
                           DimExpr M, DimExpr N, DimExpr K, DimExpr lda, DimExpr ldb, DimExpr ldc,
-                          bool accumulate = false) {
+                          bool accumulate = false, double alpha = 1.0) {
   GemmDesc d{};
   d.A = A;
   d.B = B;
@@ -161,7 +161,7 @@ static GemmDesc make_desc(const int* dims, const double2* A, int opA, const doub
   d.ldc = ldc;
   d.opA = opA;
   d.opB = opB;
-  d.alpha = make_double2(1.0, 0.0);
+  d.alpha = make_double2(alpha, 0.0);
   d.beta = make_double2(accumulate ? 1.0 : 0.0, 0.0);
   return d;
 }
@@ -183,7 +183,7 @@ static mps_status forward_gate(Ctx& cx, StateBuf& sb, int b, const double2* Gt, 
                   cx.st);
   SvdArgs a{};
   a.A = w.A.as<double2>();
-  a.Vw = w.Vw.as<double2>();
+  a.scratch = w.svd.as<double2>();
   a.dims = sb.dims;
   a.b = b;
   a.D = cx.cfg->max_bond;
@@ -196,7 +196,7 @@ static mps_status forward_gate(Ctx& cx, StateBuf& sb, int b, const double2* Gt, 
   a.lam_left = sb.lam + L.lam_off[b];
   a.lam_left_copy = tp ? tp->lamL : nullptr;
   a.status = cx.status;
-  launch_svd(a, cx.st);
+  launch_svd(a, 2 * L.cap[b], 2 * L.cap[b + 2], cx.st);
   GemmBatch g{};
   g.count = 1;
   g.d[0] = make_desc(sb.dims, C, OP_N, Vs, OP_T, Bl, dref(b, 2), dref(b + 1), dref(b + 2, 2), dref(b + 2, 2),
@@ -223,10 +223,10 @@ static mps_status reverse_gate(Ctx& cx, int t, int b, const TapeSlot& tp, double
   const Layout& L = *cx.L;
   Workspace& w = *cx.ws;
   const int* td = tp.dims;
-  const DimExpr m = dref(0, 2), Dm = dref(1), nc = dref(2, 2), k = dref(3);
+  const DimExpr m = dref(0, 2), Dm = dref(1), nc = dref(2, 2), k = dref(3), Ks = dref(4);
   double2* Bbl = Bbar + L.site_off[b];
   double2* Bbr = Bbar + L.site_off[b + 1];
-  const int mcap = 2 * L.cap[b], ncap = 2 * L.cap[b + 2], kcap = L.cap[b + 1];
+  const int mcap = 2 * L.cap[b], ncap = 2 * L.cap[b + 2], kcap = L.cap[b + 1], Kcap = std::min(mcap, ncap);
   launch_conjT(Bbr, td, w.Vbar, kcap, ncap, cx.st);                          // Vbar = Bbar_{b+1}^H
   GemmBatch g{};
   g.count = 3;
@@ -234,14 +234,19 @@ static mps_status reverse_gate(Ctx& cx, int t, int b, const TapeSlot& tp, double
   g.d[1] = make_desc(td, Bbl, OP_N, tp.Vs, OP_C, w.Cbar, m, nc, k, k, nc, nc);         // Cbar = Bbar_b V_k^H
   g.d[2] = make_desc(td, tp.Bl, OP_N, tp.Br, OP_N, w.Theta, m, nc, Dm, Dm, nc, nc);    // Theta = B_b B_{b+1}
   launch_zgemm_small(g, std::max(mcap, ncap), std::max(kcap, ncap), cx.st);
-  launch_sbar(lambar + L.lam_off[b + 1], tp.s, td, w.wbar, ncap, cx.st);              // sbar -> wbar
+  launch_sbar(lambar + L.lam_off[b + 1], tp.s, td, w.wbar, Kcap, cx.st);              // sbar -> wbar
   g.count = 1;
-  g.d[0] = make_desc(td, tp.Vs, OP_C, w.Vbar, OP_N, w.Y, nc, k, nc, nc, k, k);         // Y = V^H Vbar
+  g.d[0] = make_desc(td, tp.Vs, OP_C, w.Vbar, OP_N, w.Y, Ks, k, nc, nc, k, k);         // Y = V_e^H Vbar
+  launch_zgemm_small(g, Kcap, kcap, cx.st);
+  g.d[0] = make_desc(td, tp.Vs, OP_T, w.Y, OP_N, w.Vbar, nc, k, Ks, nc, k, k, true, -1.0);   // Z = Vbar - V_e Y
   launch_zgemm_small(g, ncap, kcap, cx.st);
-  launch_build_K(w.Y, tp.s, w.wbar, td, w.Km, ncap, cx.st);                            // diag(wbar)+J+J^H
-  g.d[0] = make_desc(td, tp.W, OP_T, w.Km, OP_N, w.T1, m, nc, nc, m, nc, nc);           // T1 = (C~ V) K
+  launch_build_K(w.Y, tp.s, w.wbar, td, w.Km, Kcap, cx.st);                            // diag(wbar)+J+J^H
+  launch_zscale(w.Vbar, tp.s, td, ncap, kcap, cx.st);                                  // Z diag(1/w_k)
+  g.d[0] = make_desc(td, tp.W, OP_T, w.Km, OP_N, w.T1, m, Ks, Ks, m, Ks, Ks);          // T1 = W K
+  launch_zgemm_small(g, mcap, Kcap, cx.st);
+  g.d[0] = make_desc(td, w.T1, OP_N, tp.Vs, OP_C, w.Ctbar, m, nc, Ks, Ks, nc, nc);     // C~bar = T1 V_e^H
   launch_zgemm_small(g, mcap, ncap, cx.st);
-  g.d[0] = make_desc(td, w.T1, OP_N, tp.Vs, OP_C, w.Ctbar, m, nc, nc, nc, nc, nc);     // C~bar = T1 V^H
+  g.d[0] = make_desc(td, tp.W, OP_T, w.Vbar, OP_H, w.Ctbar, m, nc, k, m, k, nc, true);  // += W_k (Z/w)^H
   launch_zgemm_small(g, mcap, ncap, cx.st);
   launch_lam_scale(w.Cbar, w.Ctbar, tp.C, tp.lamL, td, b > 0 ? lambar + L.lam_off[b] : nullptr, L.cap[b],
                    cx.st);
@@ -1113,45 +1118,45 @@ mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, doub
   if (m < 2 || ncol < 2 || (m & 1) || (ncol & 1) || m > 512 || ncol > 512)
     return fail(MPS_EINVAL, "mps_svd: m and ncol must be even and in 2..512");
   if (D < 1 || !(eps >= 0.0)) return fail(MPS_EINVAL, "mps_svd: bad D or eps");
-  const size_t mn = (size_t)m * ncol, nn = (size_t)ncol * ncol;
+  const size_t mn = (size_t)m * ncol, Kc = (size_t)std::min(m, ncol);
   DevBuf buf, status;
-  const size_t bytes = align256(mn * 16) * 3 + align256(nn * 16) * 2 + align256(ncol * 8) * 2 + 256 + 256;
+  const size_t sizes[] = {mn * 16, mn * 16, Kc * m * 16, Kc * ncol * 16, 2 * mn * 16 + Kc * Kc * 16,
+                          Kc * 8, Kc * 8, 256, (size_t)m * 8};
+  size_t bytes = 0;
+  for (size_t z : sizes) bytes += align256(z);
   MPS_TRY(buf.alloc(bytes));
   MPS_TRY(status.alloc(sizeof(int)));
   char* p = buf.as<char>();
-  auto take = [&](size_t b) {
+  int part = 0;
+  auto take = [&]() {
     char* q = p;
-    p += align256(b);
+    p += align256(sizes[part++]);
     return q;
   };
-  double2* Ain = reinterpret_cast<double2*>(take(mn * 16));
-  double2* Acm = reinterpret_cast<double2*>(take(mn * 16));
-  double2* W = reinterpret_cast<double2*>(take(mn * 16));
-  double2* Vw = reinterpret_cast<double2*>(take(nn * 16));
-  double2* Vs = reinterpret_cast<double2*>(take(nn * 16));
-  double* s = reinterpret_cast<double*>(take(ncol * 8));
-  double* lam = reinterpret_cast<double*>(take(ncol * 8));
-  int* dims = reinterpret_cast<int*>(take(256));
-  double* one = reinterpret_cast<double*>(take(256));
+  double2* Ain = reinterpret_cast<double2*>(take());
+  double2* Acm = reinterpret_cast<double2*>(take());
+  double2* W = reinterpret_cast<double2*>(take());
+  double2* Vs = reinterpret_cast<double2*>(take());
+  double2* scratch = reinterpret_cast<double2*>(take());
+  double* s = reinterpret_cast<double*>(take());
+  double* lam = reinterpret_cast<double*>(take());
+  int* dims = reinterpret_cast<int*>(take());
+  double* one = reinterpret_cast<double*>(take());
   const bool dev_in = is_device_ptr(A);
   MPS_CU(cudaMemcpy(Ain, A, mn * 16, dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
   int hd[3] = {m / 2, 1, ncol / 2};
   MPS_CU(cudaMemcpy(dims, hd, sizeof(hd), cudaMemcpyHostToDevice));
   std::vector<double> ones(m / 2, 1.0);
   MPS_CU(cudaMemcpy(one, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice));
-  // row-major -> column-major working copy: GEMM with the identity would do, a transpose is enough
-  GemmBatch g{};
-  g.count = 1;
-  std::vector<double2> eye(nn, make_double2(0, 0));
-  for (int i = 0; i < ncol; ++i) eye[(size_t)i * ncol + i] = make_double2(1, 0);
-  MPS_CU(cudaMemcpy(Vs, eye.data(), nn * 16, cudaMemcpyHostToDevice));
-  // Acm (ncol x m row-major) = I (ncol x ncol) * Ain^T  -> column-major A
-  g.d[0] = make_desc(dims, Vs, OP_N, Ain, OP_T, Acm, dconst(ncol), dconst(m), dconst(ncol), dconst(ncol), dconst(ncol),
-                     dconst(m));
-  launch_zgemm_small(g, ncol, m, 0);
+  // row-major input -> column-major working copy (host transpose)
+  std::vector<double2> hin(mn), hcm(mn);
+  MPS_CU(cudaMemcpy(hin.data(), Ain, mn * 16, cudaMemcpyDeviceToHost));
+  for (int r = 0; r < m; ++r)
+    for (int c = 0; c < ncol; ++c) hcm[(size_t)c * m + r] = hin[(size_t)r * ncol + c];
+  MPS_CU(cudaMemcpy(Acm, hcm.data(), mn * 16, cudaMemcpyHostToDevice));
   SvdArgs a{};
   a.A = Acm;
-  a.Vw = Vw;
+  a.scratch = scratch;
   a.dims = dims;
   a.b = 0;
   a.D = D;
@@ -1164,7 +1169,7 @@ mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, doub
   a.lam_left = one;
   a.lam_left_copy = nullptr;
   a.status = status.as<int>();
-  launch_svd(a, 0);
+  launch_svd(a, m, ncol, 0);
   MPS_CU(cudaGetLastError());
   MPS_CU(cudaDeviceSynchronize());
   int code = 0, k = 0;
@@ -1172,22 +1177,22 @@ mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, doub
   if (code) return fail((mps_status)code, "mps_svd: device status");
   MPS_CU(cudaMemcpy(&k, dims + 1, sizeof(int), cudaMemcpyDeviceToHost));
   // Vs, W are column-major (column j contiguous); return them row-major
-  std::vector<double2> hV(nn), hW(mn), tV(nn), tW(mn);
-  MPS_CU(cudaMemcpy(hV.data(), Vs, nn * 16, cudaMemcpyDeviceToHost));
-  MPS_CU(cudaMemcpy(hW.data(), W, mn * 16, cudaMemcpyDeviceToHost));
-  for (int j = 0; j < ncol; ++j) {
-    for (int r = 0; r < ncol; ++r) tV[(size_t)r * ncol + j] = hV[(size_t)j * ncol + r];
-    for (int r = 0; r < m; ++r) tW[(size_t)r * ncol + j] = hW[(size_t)j * m + r];
+  std::vector<double2> hV(Kc * ncol), hW(Kc * m), tV(Kc * ncol), tW(Kc * m);
+  MPS_CU(cudaMemcpy(hV.data(), Vs, Kc * ncol * 16, cudaMemcpyDeviceToHost));
+  MPS_CU(cudaMemcpy(hW.data(), W, Kc * m * 16, cudaMemcpyDeviceToHost));
+  for (size_t j = 0; j < Kc; ++j) {
+    for (int r = 0; r < ncol; ++r) tV[(size_t)r * Kc + j] = hV[j * ncol + r];
+    for (int r = 0; r < m; ++r) tW[(size_t)r * Kc + j] = hW[j * m + r];
   }
   auto out = [&](void* dst, const void* src, size_t b) -> mps_status {
     MPS_CU(cudaMemcpy(dst, src, b, is_device_ptr(dst) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
     return MPS_OK;
   };
-  std::vector<double> hs(ncol);
-  MPS_CU(cudaMemcpy(hs.data(), s, ncol * 8, cudaMemcpyDeviceToHost));
-  MPS_TRY(out(s_out, hs.data(), ncol * 8));
-  MPS_TRY(out(V_out, tV.data(), nn * 16));
-  MPS_TRY(out(W_out, tW.data(), mn * 16));
+  std::vector<double> hs(Kc);
+  MPS_CU(cudaMemcpy(hs.data(), s, Kc * 8, cudaMemcpyDeviceToHost));
+  MPS_TRY(out(s_out, hs.data(), Kc * 8));
+  MPS_TRY(out(V_out, tV.data(), Kc * ncol * 16));
+  MPS_TRY(out(W_out, tW.data(), Kc * m * 16));
   MPS_TRY(out(k_out, &k, sizeof(int)));
   return MPS_OK;
 }
@@ -1231,8 +1236,9 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
   // tape arena for the largest segment
   auto slot_elems = [&](int b, size_t* cplx, size_t* dbl) {
     const size_t Dl = L.cap[b], Dm = L.cap[b + 1], Dr = L.cap[b + 2], m = 2 * Dl, nc = 2 * Dr;
-    *cplx = Dl * 2 * Dm + Dm * 2 * Dr + 2 * m * nc + nc * nc;
-    *dbl = nc + Dl + 2;   // s, lambda_left, dims (4 ints)
+    const size_t Kc = std::min(m, nc);
+    *cplx = Dl * 2 * Dm + Dm * 2 * Dr + m * nc + m * Kc + nc * Kc;   // Bl, Br, C, W, Vs
+    *dbl = Kc + Dl + 4;   // s, lambda_left, dims (8 ints)
   };
   size_t arena = 0;
   for (int seg = 0; seg < nseg; ++seg) {
@@ -1288,6 +1294,7 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
     for (int t = g0; t < g1; ++t) {
       const int b = c->host[t].bond;
       const size_t Dl = L.cap[b], Dm = L.cap[b + 1], Dr = L.cap[b + 2], m = 2 * Dl, ncol = 2 * Dr;
+      const size_t Kc = std::min(m, ncol);
       size_t cp, db;
       slot_elems(b, &cp, &db);
       TapeSlot& tp = tapes[t - g0];
@@ -1296,12 +1303,12 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
       tp.Br = tp.Bl + Dl * 2 * Dm;
       tp.C = tp.Br + Dm * 2 * Dr;
       tp.W = tp.C + m * ncol;
-      tp.Vs = tp.W + m * ncol;
+      tp.Vs = tp.W + m * Kc;
       p += align256(cp * sizeof(double2));
       double* dd = reinterpret_cast<double*>(p);
       tp.s = dd;
-      tp.lamL = dd + ncol;
-      tp.dims = reinterpret_cast<int*>(dd + ncol + Dl);
+      tp.lamL = dd + Kc;
+      tp.dims = reinterpret_cast<int*>(dd + Kc + Dl);
       p += align256(db * sizeof(double));
     }
     MPS_TRY(w.rec.copy_from(*w.snaps[seg], L, s->st));

@@ -177,3 +177,58 @@ def test_invalid_arguments_are_reported(M):
         M.State.product([1, 0, 1, 0], 0, 1e-12)               # D < 1
     E, g = M.energy_grad(st, circ, th, ham)                   # the handle still works
     assert np.isfinite(E)
+
+
+@pytest.mark.parametrize("shape,rank", [((4, 4), 2), ((8, 32), 5), ((32, 8), 8), ((64, 64), 64), ((128, 96), 40),
+                                        ((96, 128), 96), ((256, 256), 256), ((128, 512), 100)])
+def test_gpu_svd_against_lapack(M, shape, rank):
+    """Steps S3-S4 on their own: singular values, orthonormal V, W = A V, truncation count."""
+    rng = np.random.default_rng(sum(shape) + rank)
+    m, n = shape
+    A = (rng.standard_normal((m, rank)) + 1j * rng.standard_normal((m, rank))) @ (
+        rng.standard_normal((rank, n)) + 1j * rng.standard_normal((rank, n)))
+    D = 1000
+    s, V, W, k = M.svd(A, D, 1e-12)
+    sl = np.linalg.svd(A, compute_uv=False)
+    K = min(m, n)
+    assert s.shape == (K,) and V.shape == (n, K) and W.shape == (m, K)
+    assert np.abs(s - sl).max() <= 1e-12 * sl[0]
+    Vr = V[:, :rank]
+    assert np.abs(Vr.conj().T @ Vr - np.eye(rank)).max() < 1e-12
+    assert np.abs(W[:, :rank] - A @ Vr).max() < 1e-12 * sl[0]
+    assert np.abs(W[:, rank:]).max(initial=0.0) == 0.0          # numerical zeros are stored as zeros
+    if m >= n:                                                  # tall: V is the full unitary
+        assert np.abs(V.conj().T @ V - np.eye(n)).max() < 1e-12
+    assert k == rank
+
+
+def test_gpu_svd_truncation_rule(M):
+    s_true = np.array([1.0, 0.5, 1e-3, 1e-9, 1e-11, 1e-13])
+    rng = np.random.default_rng(1)
+    Q1, _ = np.linalg.qr(rng.standard_normal((6, 6)) + 1j * rng.standard_normal((6, 6)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((6, 6)) + 1j * rng.standard_normal((6, 6)))
+    A = Q1 @ np.diag(s_true) @ Q2
+    # eps = 0 keeps everything above the numerical-zero level 1e-13 s_1 (so not the 1e-13 value)
+    for D, eps, want in [(64, 1e-10, 4), (64, 1e-12, 5), (3, 1e-12, 3), (64, 0.6, 1), (64, 0.0, 5)]:
+        assert M.svd(A, D, eps)[3] == want
+
+
+@pytest.mark.parametrize("case", ["cfg0", "n8_trunc", "cfg1_prefix"])
+def test_energy_cotangent_matches_oracle(M, case):
+    """Step S7: dE/dB* of the final state against the oracle's plain per-string definition."""
+    if case == "cfg0":
+        p, excs, D, eps = S.make_problem(0), None, None, None
+    elif case == "n8_trunc":
+        p, D, eps = small(D=4, eps=1e-10), 4, 1e-10
+        excs = p.excitations[:12]
+    else:
+        p = S.make_problem(1)
+        excs, D, eps = p.excitations[:25], None, None
+    st, circ, ham, th = prepare(M, p, excs, D, eps)
+    M.apply_circuit(st, circ, th)
+    dims, lams, B = st.read()
+    E, Bbar = M.energy_cotangent(st, ham)
+    Eo, Bo = OM.energy_seed(OM.MPS(B, lams), pauli.jw_hamiltonian(p.h, p.eri))
+    assert abs(E - Eo) <= E_TOL * max(1.0, abs(Eo))
+    scale = max(np.abs(b).max() for b in Bo)
+    assert max(np.abs(a - b).max() for a, b in zip(Bbar, Bo)) <= 1e-11 * scale
