@@ -51,7 +51,9 @@ typedef struct {
   double cutoff;             /* eps: keep singular values with s_i/||s||_2 > eps (values
                                 at or below 1e-13 s_1 are numerical zeros, never kept) */
   int32_t precision;         /* MPS_PRECISION_FP64 (only value accepted by this build) */
-  int32_t checkpoint_every;  /* reverse pass: MPS snapshot every k gates; 0 = 512 */
+  int32_t checkpoint_every;  /* reverse pass: MPS snapshot every k gates, the segment
+                                re-run with a tape; 0 = automatic: one tape for the whole
+                                circuit when it fits in 40% of free device memory, else 512 */
   void* cuda_stream;         /* cudaStream_t, NULL = default stream */
 } mps_config;
 
@@ -209,6 +211,16 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
  */
 mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, double eps, double* s_out,
                        double* V_out, double* W_out, int32_t* k_out);
+
+/*
+ * Profiling of the gate SVD, the dominant kernel.  While enabled, every SVD launch of calls on
+ * this state is bracketed by CUDA events on the state's stream and the SVD kernel adds the
+ * floating-point operations its sweeps actually performed to a device counter.
+ * mps_profile_read returns {total SVD time in ms, SVD launches, FP64 flops, FP32 flops} since
+ * the last read and resets them.  The library has no counterpart in the paper.
+ */
+mps_status mps_profile(mps_state* s, int32_t enable);
+mps_status mps_profile_read(mps_state* s, double* out4);
 
 /* Release a state (NULL-safe). */
 void mps_free(mps_state* s);

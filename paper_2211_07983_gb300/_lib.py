@@ -72,6 +72,8 @@ _SIGS = {
                                       c_void_p]),
     "mps_svd_dev": (c_int32, [c_int32, c_int32, c_void_p, c_int32, c_double, c_void_p, c_void_p, c_void_p,
                               c_void_p]),
+    "mps_profile": (c_int32, [c_void_p, c_int32]),
+    "mps_profile_read": (c_int32, [c_void_p, c_void_p]),
     "mps_free": (None, [c_void_p]),
     "mps_last_error": (ctypes.c_char_p, []),
     "mps_kernel_launches": (c_int64, []),

@@ -132,6 +132,17 @@ class State:
             o += e
         return dims, lams, B
 
+    def profile(self, enable: bool = True) -> None:
+        """mps_profile: time every gate SVD with CUDA events and count its flops."""
+        check(_lib.load().mps_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """mps_profile_read: SVD time (ms), launches, FP64 and FP32 flops since the last read."""
+        out = np.zeros(4)
+        check(_lib.load().mps_profile_read(self._h, _ptr(out)))
+        return {"svd_ms": float(out[0]), "svd_launches": int(out[1]), "fp64_flops": float(out[2]),
+                "fp32_flops": float(out[3])}
+
     def free(self):
         if self._h is not None and self._h.value:
             _lib.load().mps_free(self._h)

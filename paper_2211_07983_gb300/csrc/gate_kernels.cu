@@ -131,17 +131,29 @@ struct Cplx<float> {
 };
 
 // Cyclic (round-robin) sweeps over the K columns of X (R rows, column j at X + j*R) with the
-// rotations accumulated into Q (K x K, column j at Q + j*K).  One warp per column pair.
+// rotations accumulated into Q (K x K, column j at Q + j*K).  One warp per column pair.  Column
+// norms are recomputed at the start of every sweep and updated by each rotation
+// (alpha' = alpha - t g, beta' = beta + t g), so a pair costs one inner product.
 // Returns the number of sweeps run; *converged = 1 if the last sweep rotated nothing.
 template <class T>
 __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int R, int K, T tol, T tiny,
-                             int max_sweeps, int* flag_sh, int* converged) {
+                             int max_sweeps, int* flag_sh, int* converged, T* nrm, double* flops) {
   using C2 = typename Cplx<T>::t;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   const int Kp = K + (K & 1);
   int sweep = 0;
+  long long checks = 0, rots = 0;   // per warp (lane 0's count is used)
   *converged = 0;
   for (; sweep < max_sweeps; ++sweep) {
+    for (int j = warp; j < K; j += nwarp) {
+      T v = 0;
+      for (int i = lane; i < R; i += 32) {
+        const C2 x = X[(size_t)j * R + i];
+        v += x.x * x.x + x.y * x.y;
+      }
+      v = Cplx<T>::sum(v);
+      if (lane == 0) nrm[j] = v;
+    }
     if (tid == 0) *flag_sh = 0;
     __syncthreads();
     for (int r = 0; r < Kp - 1; ++r) {
@@ -155,21 +167,19 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
           qc = (r - t + Kp - 1) % (Kp - 1);
         }
         if (pc >= K || qc >= K) continue;
+        const T al = nrm[pc], be = nrm[qc];
+        if (al < tiny || be < tiny) continue;
         C2* ap = X + (size_t)pc * R;
         C2* aq = X + (size_t)qc * R;
-        T al = 0, be = 0, gr = 0, gi = 0;
+        ++checks;
+        T gr = 0, gi = 0;
         for (int i = lane; i < R; i += 32) {
           const C2 x = ap[i], y = aq[i];
-          al += x.x * x.x + x.y * x.y;
-          be += y.x * y.x + y.y * y.y;
           gr += x.x * y.x + x.y * y.y;   // conj(x) y
           gi += x.x * y.y - x.y * y.x;
         }
-        al = Cplx<T>::sum(al);
-        be = Cplx<T>::sum(be);
         gr = Cplx<T>::sum(gr);
         gi = Cplx<T>::sum(gi);
-        if (al < tiny || be < tiny) continue;
         const T g = hypot(gr, gi);
         if (!(g > tol * sqrt(al) * sqrt(be))) continue;
         const T zeta = (be - al) / (T(2) * g);
@@ -190,7 +200,12 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
           vp[i] = Cplx<T>::mk(c * x.x - (spr * y.x + spi * y.y), c * x.y - (spr * y.y - spi * y.x));
           vq[i] = Cplx<T>::mk(spr * x.x - spi * x.y + c * y.x, spr * x.y + spi * x.x + c * y.y);
         }
-        if (lane == 0) *flag_sh = 1;
+        ++rots;
+        if (lane == 0) {
+          nrm[pc] = al - tt * g;
+          nrm[qc] = be + tt * g;
+          *flag_sh = 1;
+        }
       }
       __syncthreads();
     }
@@ -198,8 +213,16 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
     __syncthreads();
     if (!rot) {
       *converged = 1;
-      return sweep + 1;
+      ++sweep;
+      break;
     }
+  }
+  // work actually done: per sweep K column norms (4R flops each), per checked pair one complex
+  // inner product (8R), per rotation the update of two columns of X (24R) and of Q (24K)
+  if (flops && lane == 0) {
+    double f = 8.0 * R * (double)checks + (24.0 * R + 24.0 * K) * (double)rots;
+    if (warp == 0) f += 4.0 * R * K * (double)sweep;
+    atomicAdd(flops, f);
   }
   return sweep;
 }
@@ -245,7 +268,7 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(SvdArgs p) {
   __syncthreads();
   int conv = 0;
   jacobi_sweeps<float>(X32, Q32, R, K, 4.f * 1.1920929e-7f * sqrtf((float)R), (float)(1e-30 * fro2_sh) + 1e-37f,
-                       30, &flag_sh, &conv);
+                       30, &flag_sh, &conv, reinterpret_cast<float*>(s_sh), p.stats ? p.stats + 1 : nullptr);
   // ---- Q64 = orthonormalised Q32 (modified Gram-Schmidt, FP64) ----
   for (int e = tid; e < K * K; e += SVD_THREADS) Q64[e] = make_double2((double)Q32[e].x, (double)Q32[e].y);
   __syncthreads();
@@ -284,7 +307,9 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(SvdArgs p) {
   __syncthreads();
   // ---- FP64 sweeps ----
   jacobi_sweeps<double>(X64, Q64, R, K, 4.0 * 2.220446049250313e-16 * sqrt((double)R), 1e-30 * fro2_sh,
-                        SVD_MAX_SWEEPS, &flag_sh, &conv_sh);
+                        SVD_MAX_SWEEPS, &flag_sh, &conv_sh, s_sh, p.stats);
+  // FP64 work outside the sweeps: Gram-Schmidt (~8 K^3) and X = X0 Q (8 R K^2)
+  if (p.stats && tid == 0) atomicAdd(p.stats, 8.0 * K * K * (double)K + 8.0 * R * K * (double)K);
   if (tid == 0 && !conv_sh) set_status(p.status, MPS_ENOCONV);
   // ---- singular values, order, outputs ----
   for (int j = warp; j < K; j += nwarp) {
@@ -555,24 +580,25 @@ size_t svd_smem_bytes(int m_cap, int n_cap) {
 
 // Largest dynamic shared memory the SVD kernel may use: the device's opt-in limit per block minus
 // the kernel's static shared memory (queried once; 0 if the attribute cannot be raised).
-static size_t svd_dynamic_limit() {
-  static size_t limit = (size_t)-1;
-  if (limit != (size_t)-1) return limit;
+static size_t svd_dynamic_limit_query() {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaFuncAttributes fa{};
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
       cudaFuncGetAttributes(&fa, svd_kernel) != cudaSuccess) {
     cudaGetLastError();
-    limit = 0;
-    return limit;
+    return 0;
   }
   size_t want = (size_t)optin > fa.sharedSizeBytes + 1024 ? (size_t)optin - fa.sharedSizeBytes - 1024 : 0;
   if (cudaFuncSetAttribute(svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)want) != cudaSuccess) {
     cudaGetLastError();
     want = 48 * 1024 > fa.sharedSizeBytes ? 48 * 1024 - fa.sharedSizeBytes : 0;
   }
-  limit = want;
+  return want;
+}
+
+static size_t svd_dynamic_limit() {
+  static const size_t limit = svd_dynamic_limit_query();   // thread-safe one-time initialisation
   return limit;
 }
 

@@ -55,6 +55,7 @@ struct SvdArgs {
   const double* lam_left;
   double* lam_left_copy;
   int* status;
+  double* stats;   // optional: [0] += FP64 flops, [1] += FP32 flops performed
 };
 size_t svd_smem_bytes(int m_cap, int n_cap);
 bool svd_fits_smem(int m_cap, int n_cap);

@@ -125,6 +125,16 @@ struct Workspace {
           *Theta = nullptr, *Thbar = nullptr, *Gbar = nullptr;
   double* wbar = nullptr;
   bool work_ok = false;
+  // profiling of the gate SVD (mps_profile): events around every launch, flop counters
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  DevBuf stats;            // 2 doubles on the device
+  double svd_ms = 0.0;
+  long long svd_launches = 0;
+  ~Workspace() {
+    for (auto e : ev_pool) cudaEventDestroy(e);
+  }
 };
 
 struct Ctx {
@@ -196,7 +206,22 @@ static mps_status forward_gate(Ctx& cx, StateBuf& sb, int b, const double2* Gt, 
   a.lam_left = sb.lam + L.lam_off[b];
   a.lam_left_copy = tp ? tp->lamL : nullptr;
   a.status = cx.status;
+  a.stats = w.profile ? w.stats.as<double>() : nullptr;
+  if (w.profile) {
+    if (w.ev_used + 2 > w.ev_pool.size()) {
+      for (int q = 0; q < 256; ++q) {
+        cudaEvent_t e;
+        MPS_CU(cudaEventCreate(&e));
+        w.ev_pool.push_back(e);
+      }
+    }
+    MPS_CU(cudaEventRecord(w.ev_pool[w.ev_used], cx.st));
+  }
   launch_svd(a, 2 * L.cap[b], 2 * L.cap[b + 2], cx.st);
+  if (w.profile) {
+    MPS_CU(cudaEventRecord(w.ev_pool[w.ev_used + 1], cx.st));
+    w.ev_used += 2;
+  }
   GemmBatch g{};
   g.count = 1;
   g.d[0] = make_desc(sb.dims, C, OP_N, Vs, OP_T, Bl, dref(b, 2), dref(b + 1), dref(b + 2, 2), dref(b + 2, 2),
@@ -781,6 +806,18 @@ static mps_status build_trie(mps_hamiltonian_dev* h) {
   return MPS_OK;
 }
 
+// Sum the durations of the profiled SVD launches of the finished call (stream already idle).
+static mps_status harvest_profile(Workspace& w) {
+  for (size_t i = 0; i + 1 < w.ev_used; i += 2) {
+    float ms = 0.f;
+    MPS_CU(cudaEventElapsedTime(&ms, w.ev_pool[i], w.ev_pool[i + 1]));
+    w.svd_ms += ms;
+    ++w.svd_launches;
+  }
+  w.ev_used = 0;
+  return MPS_OK;
+}
+
 mps_status check_status_word(cudaStream_t st, DevBuf& status, const char* where) {
   MPS_CU(cudaStreamSynchronize(st));
   int code = 0;
@@ -872,8 +909,7 @@ mps_status mps_init_product(int32_t n_qubits, const uint8_t* bits, const mps_con
   for (int i = 0; i < n_qubits; ++i)
     if (bits[i] > 1) return fail(MPS_EINVAL, "mps_init_product: bits must be 0 or 1");
   std::unique_ptr<mps_state> s(new mps_state());
-  s->cfg = *cfg;
-  if (s->cfg.checkpoint_every == 0) s->cfg.checkpoint_every = 512;
+  s->cfg = *cfg;   // checkpoint_every == 0: automatic (whole-circuit tape when it fits)
   s->st = (cudaStream_t)cfg->cuda_stream;
   s->L.build(n_qubits, cfg->max_bond);
   s->ws.reset(new Workspace());
@@ -905,6 +941,34 @@ mps_status mps_clone(const mps_state* s, mps_state** out) {
   MPS_TRY(c->buf.copy_from(s->buf, s->L, s->st));
   MPS_CU(cudaStreamSynchronize(s->st));
   *out = c.release();
+  return MPS_OK;
+}
+
+mps_status mps_profile(mps_state* s, int32_t enable) {
+  clear_error();
+  if (!s) return fail(MPS_EINVAL, "mps_profile: state is NULL");
+  Workspace& w = *s->ws;
+  MPS_TRY(w.stats.ensure(2 * sizeof(double)));
+  w.profile = enable != 0;
+  return MPS_OK;
+}
+
+mps_status mps_profile_read(mps_state* s, double* out4) {
+  clear_error();
+  if (!s || !out4) return fail(MPS_EINVAL, "mps_profile_read: NULL argument");
+  Workspace& w = *s->ws;
+  double fl[2] = {0.0, 0.0};
+  if (w.stats.p) {
+    MPS_CU(cudaStreamSynchronize(s->st));
+    MPS_CU(cudaMemcpy(fl, w.stats.p, sizeof(fl), cudaMemcpyDeviceToHost));
+    MPS_CU(cudaMemset(w.stats.p, 0, sizeof(fl)));
+  }
+  out4[0] = w.svd_ms;
+  out4[1] = (double)w.svd_launches;
+  out4[2] = fl[0];
+  out4[3] = fl[1];
+  w.svd_ms = 0.0;
+  w.svd_launches = 0;
   return MPS_OK;
 }
 
@@ -1050,9 +1114,11 @@ mps_status mps_apply_circuit_dev(mps_state* s, const mps_circuit* c, const doubl
   MPS_TRY(stage_theta(s, theta, n_theta, &d_theta));
   MPS_TRY(ensure_forward_scratch(s->L, *s->ws));
   MPS_TRY(gate_matrices(s, c, d_theta, n_theta));
+  s->ws->ev_used = 0;
   Ctx cx{&s->L, &s->cfg, s->st, s->status.as<int>(), s->ws.get()};
   MPS_TRY(forward_gates(cx, s->buf, c, s->ws->G.as<double2>(), 0, c->n_gates, nullptr));
-  return check_status_word(s->st, s->status, "mps_apply_circuit");
+  MPS_TRY(check_status_word(s->st, s->status, "mps_apply_circuit"));
+  return harvest_profile(*s->ws);
 }
 
 mps_status mps_apply_circuit(mps_state* s, const mps_gate* gates, int32_t n_gates, const double* theta,
@@ -1221,33 +1287,44 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
   MPS_TRY(stage_theta(s, theta, n_theta, &d_theta));
   MPS_TRY(ensure_forward_scratch(L, w));
   MPS_TRY(gate_matrices(s, c, d_theta, n_theta));
+  w.ev_used = 0;
   const int ng = c->n_gates;
-  const int K = std::max(1, s->cfg.checkpoint_every);
-  const int nseg = (ng + K - 1) / K;
-  if (!w.work_ok) {
-    MPS_TRY(w.work.alloc(L));
-    MPS_TRY(w.rec.alloc(L));
-    w.work_ok = true;
-  }
-  while ((int)w.snaps.size() < nseg) {
-    w.snaps.emplace_back(new StateBuf());
-    MPS_TRY(w.snaps.back()->alloc(L));
-  }
-  // tape arena for the largest segment
+  // tape slot of one gate: pre-gate tensors, C, W, V, s, lambda_left, dims
   auto slot_elems = [&](int b, size_t* cplx, size_t* dbl) {
     const size_t Dl = L.cap[b], Dm = L.cap[b + 1], Dr = L.cap[b + 2], m = 2 * Dl, nc = 2 * Dr;
     const size_t Kc = std::min(m, nc);
     *cplx = Dl * 2 * Dm + Dm * 2 * Dr + m * nc + m * Kc + nc * Kc;   // Bl, Br, C, W, Vs
     *dbl = Kc + Dl + 4;   // s, lambda_left, dims (8 ints)
   };
+  auto slot_bytes = [&](int b) {
+    size_t cp, db;
+    slot_elems(b, &cp, &db);
+    return align256(cp * sizeof(double2)) + align256(db * sizeof(double));
+  };
+  int K = s->cfg.checkpoint_every;
+  if (K <= 0) {   // automatic: keep the tape of the whole circuit when it takes < 40% of free memory
+    size_t all = 0;
+    for (int t = 0; t < ng; ++t) all += slot_bytes(c->host[t].bond);
+    size_t fr = 0, tot = 0;
+    MPS_CU(cudaMemGetInfo(&fr, &tot));
+    K = (all + w.tape.bytes <= (size_t)(0.4 * (double)(fr + w.tape.bytes))) ? std::max(1, ng) : 512;
+  }
+  const int nseg = (ng + K - 1) / K;
+  if (!w.work_ok) {
+    MPS_TRY(w.work.alloc(L));
+    MPS_TRY(w.rec.alloc(L));
+    w.work_ok = true;
+  }
+  if (nseg > 1)
+    while ((int)w.snaps.size() < nseg) {
+      w.snaps.emplace_back(new StateBuf());
+      MPS_TRY(w.snaps.back()->alloc(L));
+    }
+  // tape arena for the largest segment
   size_t arena = 0;
   for (int seg = 0; seg < nseg; ++seg) {
     size_t tot = 0;
-    for (int t = seg * K; t < std::min(ng, (seg + 1) * K); ++t) {
-      size_t cp, db;
-      slot_elems(c->host[t].bond, &cp, &db);
-      tot += align256(cp * sizeof(double2)) + align256(db * sizeof(double));
-    }
+    for (int t = seg * K; t < std::min(ng, (seg + 1) * K); ++t) tot += slot_bytes(c->host[t].bond);
     arena = std::max(arena, tot);
   }
   MPS_TRY(w.tape.ensure(std::max<size_t>(arena, 256)));
@@ -1274,21 +1351,8 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
   Ctx cx{&L, &s->cfg, s->st, s->status.as<int>(), &w};
   const double2* G = w.G.as<double2>();
   const double2* dG = w.dG.as<double2>();
-  // forward with snapshots
-  MPS_TRY(w.work.copy_from(s->buf, L, s->st));
-  for (int seg = 0; seg < nseg; ++seg) {
-    MPS_TRY(w.snaps[seg]->copy_from(w.work, L, s->st));
-    MPS_TRY(forward_gates(cx, w.work, c, G, seg * K, std::min(ng, (seg + 1) * K), nullptr));
-  }
-  // energy and its cotangent
-  double* dE = w.scalars.as<double>();
-  MPS_TRY(energy_pass_impl(L, w.work, s->st, s->status.as<int>(), h, dE, nullptr, w.Bbar.as<double2>()));
-  MPS_CU(cudaMemsetAsync(w.lambar.p, 0, L.lam_elems() * sizeof(double), s->st));
-  MPS_CU(cudaMemsetAsync(w.gate_grad.p, 0, std::max(1, ng) * sizeof(double), s->st));
-  // reverse, segment by segment
   std::vector<TapeSlot> tapes;
-  for (int seg = nseg - 1; seg >= 0; --seg) {
-    const int g0 = seg * K, g1 = std::min(ng, (seg + 1) * K);
+  auto layout_tapes = [&](int g0, int g1) {
     tapes.assign(g1 - g0, TapeSlot{});
     char* p = w.tape.as<char>();
     for (int t = g0; t < g1; ++t) {
@@ -1311,8 +1375,32 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
       tp.dims = reinterpret_cast<int*>(dd + Kc + Dl);
       p += align256(db * sizeof(double));
     }
-    MPS_TRY(w.rec.copy_from(*w.snaps[seg], L, s->st));
-    MPS_TRY(forward_gates(cx, w.rec, c, G, g0, g1, &tapes));
+  };
+  double* dE = w.scalars.as<double>();
+  MPS_TRY(w.work.copy_from(s->buf, L, s->st));
+  if (nseg == 1) {
+    // whole-circuit tape: one forward pass records everything the reverse pass needs
+    layout_tapes(0, ng);
+    MPS_TRY(forward_gates(cx, w.work, c, G, 0, ng, &tapes));
+  } else {
+    // forward with an MPS snapshot at the start of every segment
+    for (int seg = 0; seg < nseg; ++seg) {
+      MPS_TRY(w.snaps[seg]->copy_from(w.work, L, s->st));
+      MPS_TRY(forward_gates(cx, w.work, c, G, seg * K, std::min(ng, (seg + 1) * K), nullptr));
+    }
+  }
+  // energy and its cotangent
+  MPS_TRY(energy_pass_impl(L, w.work, s->st, s->status.as<int>(), h, dE, nullptr, w.Bbar.as<double2>()));
+  MPS_CU(cudaMemsetAsync(w.lambar.p, 0, L.lam_elems() * sizeof(double), s->st));
+  MPS_CU(cudaMemsetAsync(w.gate_grad.p, 0, std::max(1, ng) * sizeof(double), s->st));
+  // reverse, segment by segment (re-running a segment's forward from its snapshot with a tape)
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int g0 = seg * K, g1 = std::min(ng, (seg + 1) * K);
+    if (nseg > 1) {
+      layout_tapes(g0, g1);
+      MPS_TRY(w.rec.copy_from(*w.snaps[seg], L, s->st));
+      MPS_TRY(forward_gates(cx, w.rec, c, G, g0, g1, &tapes));
+    }
     for (int t = g1 - 1; t >= g0; --t)
       MPS_TRY(reverse_gate(cx, t, c->host[t].bond, tapes[t - g0], w.Bbar.as<double2>(), w.lambar.as<double>(), G, dG,
                            w.gate_grad.as<double>()));
@@ -1327,7 +1415,8 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
   MPS_TRY(put_out(E_out, dE, 1, s->st));
   MPS_TRY(put_out(grad_out, w.grad.as<double>(), n_theta, s->st));
   MPS_TRY(put_out(gate_grad_out, w.gate_grad.as<double>(), ng, s->st));
-  return check_status_word(s->st, s->status, "mps_energy_grad");
+  MPS_TRY(check_status_word(s->st, s->status, "mps_energy_grad"));
+  return harvest_profile(w);
 }
 
 mps_status mps_energy_grad(const mps_state* s0, const mps_gate* gates, int32_t n_gates, const double* theta,

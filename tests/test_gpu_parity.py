@@ -203,12 +203,12 @@ def test_gpu_svd_against_lapack(M, shape, rank):
 
 
 def test_gpu_svd_truncation_rule(M):
-    s_true = np.array([1.0, 0.5, 1e-3, 1e-9, 1e-11, 1e-13])
+    s_true = np.array([1.0, 0.5, 1e-3, 1e-9, 1e-11, 1e-14])
     rng = np.random.default_rng(1)
     Q1, _ = np.linalg.qr(rng.standard_normal((6, 6)) + 1j * rng.standard_normal((6, 6)))
     Q2, _ = np.linalg.qr(rng.standard_normal((6, 6)) + 1j * rng.standard_normal((6, 6)))
     A = Q1 @ np.diag(s_true) @ Q2
-    # eps = 0 keeps everything above the numerical-zero level 1e-13 s_1 (so not the 1e-13 value)
+    # eps = 0 keeps everything above the numerical-zero level 1e-13 s_1 (so not the 1e-14 value)
     for D, eps, want in [(64, 1e-10, 4), (64, 1e-12, 5), (3, 1e-12, 3), (64, 0.6, 1), (64, 0.0, 5)]:
         assert M.svd(A, D, eps)[3] == want
 
