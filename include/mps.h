@@ -216,11 +216,14 @@ mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, doub
  * Profiling of the gate SVD, the dominant kernel.  While enabled, every SVD launch of calls on
  * this state is bracketed by CUDA events on the state's stream and the SVD kernel adds the
  * floating-point operations its sweeps actually performed to a device counter.
- * mps_profile_read returns {total SVD time in ms, SVD launches, FP64 flops, FP32 flops} since
- * the last read and resets them.  The library has no counterpart in the paper.
+ * mps_profile_read fills out6 = {SVD time in ms from the CUDA events, SVD launches timed by
+ * events, FP64 flops, FP32 flops, SVD time in ms from the kernel's own %globaltimer reads, SVD
+ * launches counted on the device} since the last read and resets them.  The flop and device-time
+ * counters run whether or not profiling is enabled (also inside captured graphs); the events only
+ * while it is enabled (calls then run without graph replay).  No counterpart in the paper.
  */
 mps_status mps_profile(mps_state* s, int32_t enable);
-mps_status mps_profile_read(mps_state* s, double* out4);
+mps_status mps_profile_read(mps_state* s, double* out6);
 
 /* Release a state (NULL-safe). */
 void mps_free(mps_state* s);

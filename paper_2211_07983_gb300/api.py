@@ -138,10 +138,10 @@ class State:
 
     def profile_read(self) -> dict:
         """mps_profile_read: SVD time (ms), launches, FP64 and FP32 flops since the last read."""
-        out = np.zeros(4)
+        out = np.zeros(6)
         check(_lib.load().mps_profile_read(self._h, _ptr(out)))
         return {"svd_ms": float(out[0]), "svd_launches": int(out[1]), "fp64_flops": float(out[2]),
-                "fp32_flops": float(out[3])}
+                "fp32_flops": float(out[3]), "svd_ms_device": float(out[4]), "svd_launches_device": int(out[5])}
 
     def free(self):
         if self._h is not None and self._h.value:

@@ -87,6 +87,7 @@ struct mps_state {
 };
 
 struct mps_circuit {
+  long long uid = 0;      // unique per created circuit (keys captured graphs)
   int n = 0, n_gates = 0, max_theta_idx = -1;
   std::vector<mps_gate> host;
   mpsi::DevBuf gates;     // mps_gate array
@@ -96,9 +97,11 @@ struct mps_circuit {
 
 namespace mpsi {
 struct EnergyCache;
+long long next_uid();
 }
 
 struct mps_hamiltonian_dev {
+  long long uid = 0;      // unique per created Hamiltonian (keys captured graphs)
   int n = 0;
   double c0 = 0.0;                         // identity-string coefficient
   std::vector<uint64_t> x, z;              // canonical order, identity excluded

@@ -227,8 +227,15 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
   return sweep;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(SvdArgs p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const unsigned long long t_start = global_ns();
   __shared__ double red[SVD_THREADS / 32];
   __shared__ double s_sh[512];
   __shared__ int flag_sh, conv_sh, k_sh;
@@ -388,6 +395,10 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(SvdArgs p) {
       p.tape_dims[4] = K;
     }
     p.dims[b + 1] = k;
+    if (p.stats) {   // device-side duration of this launch
+      atomicAdd(p.stats + 2, (double)(global_ns() - t_start));
+      atomicAdd(p.stats + 3, 1.0);
+    }
   }
 }
 

@@ -88,15 +88,47 @@ __global__ void __launch_bounds__(256) zgemm_batched_kernel(const GemmDesc* __re
   gemm_tile(descs[blockIdx.z]);
 }
 
+// Small per-gate GEMMs: 16 x 16 outputs per CTA, one per thread.  FP64 is the bound, so the
+// work is spread over as many SMs as the output allows (a 64 x 64 output uses 16 CTAs).
+constexpr int SM_T = 16, SK = 16;
+
 __global__ void __launch_bounds__(256) zgemm_small_kernel(const GemmBatch batch) {
-  gemm_tile(batch.d[blockIdx.z]);
+  const GemmDesc& d = batch.d[blockIdx.z];
+  const int M = deval(d.M, d.dims), N = deval(d.N, d.dims), K = deval(d.K, d.dims);
+  const int row0 = blockIdx.y * SM_T, col0 = blockIdx.x * SM_T;
+  if (row0 >= M || col0 >= N || M <= 0 || N <= 0) return;
+  const int lda = deval(d.lda, d.dims), ldb = deval(d.ldb, d.dims), ldc = deval(d.ldc, d.dims);
+  __shared__ double2 As[SK][SM_T + 1];
+  __shared__ double2 Bs[SK][SM_T + 1];
+  const int tx = threadIdx.x % SM_T, ty = threadIdx.x / SM_T;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < K; k0 += SK) {
+    {
+      const int kk = threadIdx.x / SM_T, ii = threadIdx.x % SM_T;   // SK x SM_T = 256 loads each
+      const int r = row0 + ii, c = k0 + kk;
+      As[kk][ii] = (r < M && c < K) ? load_op(d.A, lda, d.opA, r, c) : make_double2(0.0, 0.0);
+      const int rb = k0 + kk, cb = col0 + ii;
+      Bs[kk][ii] = (rb < K && cb < N) ? load_op(d.B, ldb, d.opB, rb, cb) : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < SK; ++kk) acc = cfma(As[kk][ty], Bs[kk][tx], acc);
+    __syncthreads();
+  }
+  const int r = row0 + ty, c = col0 + tx;
+  if (r < M && c < N) {
+    double2 v = cmul(d.alpha, acc);
+    double2* out = d.C + (size_t)r * ldc + c;
+    if (!(d.beta.x == 0.0 && d.beta.y == 0.0)) v = cadd(v, cmul(d.beta, *out));
+    *out = v;
+  }
 }
 
 }  // namespace
 
 void launch_zgemm_small(const GemmBatch& b, int max_m, int max_n, cudaStream_t st) {
   if (b.count <= 0 || max_m <= 0 || max_n <= 0) return;
-  dim3 grid((max_n + TN - 1) / TN, (max_m + TM - 1) / TM, b.count);
+  dim3 grid((max_n + SM_T - 1) / SM_T, (max_m + SM_T - 1) / SM_T, b.count);
   zgemm_small_kernel<<<grid, 256, 0, st>>>(b);
   note_launch();
 }

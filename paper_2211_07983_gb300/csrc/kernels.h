@@ -14,7 +14,9 @@
 namespace mpsk {
 
 void note_launch();
+void add_launches(long long k);
 long long launches();
+long long thread_launches();
 
 void launch_zgemm_batched(const GemmDesc* d_descs, int count, int max_m, int max_n, cudaStream_t st);
 // up to 4 descriptors passed by value (no device-side descriptor storage needed)
@@ -55,7 +57,7 @@ struct SvdArgs {
   const double* lam_left;
   double* lam_left_copy;
   int* status;
-  double* stats;   // optional: [0] += FP64 flops, [1] += FP32 flops performed
+  double* stats;   // optional: [0] += FP64 flops, [1] += FP32 flops, [2] += kernel ns, [3] += 1
 };
 size_t svd_smem_bytes(int m_cap, int n_cap);
 bool svd_fits_smem(int m_cap, int n_cap);

@@ -25,11 +25,20 @@ using namespace mpsk;
 
 namespace mpsk {
 static std::atomic<long long> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;   // launches issued by this thread (graph capture)
+void note_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
+void add_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launches() { return g_launches.load(); }
+long long thread_launches() { return t_launches; }
 }  // namespace mpsk
 
 namespace mpsi {
+
+static std::atomic<long long> g_uid{0};
+long long next_uid() { return ++g_uid; }
 
 static thread_local std::string g_err;
 
@@ -129,11 +138,16 @@ struct Workspace {
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  DevBuf stats;            // 2 doubles on the device
+  DevBuf stats;            // 4 doubles on the device: FP64 flops, FP32 flops, SVD ns, SVD launches
   double svd_ms = 0.0;
   long long svd_launches = 0;
+  // captured energy+gradient call (see mps_energy_grad_dev)
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<const void*> graph_key, graph_seen;
+  long long graph_kernels = 0;
   ~Workspace() {
     for (auto e : ev_pool) cudaEventDestroy(e);
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
   }
 };
 
@@ -206,7 +220,7 @@ static mps_status forward_gate(Ctx& cx, StateBuf& sb, int b, const double2* Gt, 
   a.lam_left = sb.lam + L.lam_off[b];
   a.lam_left_copy = tp ? tp->lamL : nullptr;
   a.status = cx.status;
-  a.stats = w.profile ? w.stats.as<double>() : nullptr;
+  a.stats = w.stats.as<double>();
   if (w.profile) {
     if (w.ev_used + 2 > w.ev_pool.size()) {
       for (int q = 0; q < 256; ++q) {
@@ -300,6 +314,7 @@ struct Step {
 struct EnergyCache {
   const void* key_B = nullptr;
   const int* key_dims = nullptr;
+  const void* key_Bbar = nullptr;
   DevBuf bufs, tables;
   std::vector<Step> plan_e, plan_seed;
   // device views
@@ -330,7 +345,7 @@ namespace mpsi {
 
 // Build every buffer, descriptor and step of the energy (+ cotangent) pass for one state layout.
 static mps_status build_energy_cache(const Layout& L, const StateBuf& sb, mps_hamiltonian_dev* h,
-                                     EnergyCache& ec) {
+                                     double2* d_Bbar, EnergyCache& ec) {
   const int n = L.n;
   const int nn = (int)h->node_site.size();
   const int nt = (int)h->x.size();
@@ -617,7 +632,7 @@ static mps_status build_energy_cache(const Layout& L, const StateBuf& sb, mps_ha
   std::vector<const double2*> Enode(nn);
   for (int v = 0; v < nn; ++v) Enode[v] = P(oE[v]);
   for (int s = 0; s < n; ++s) {
-    seeds[s].out = nullptr;   // patched per call
+    seeds[s].out = d_Bbar ? d_Bbar + L.site_off[s] : nullptr;
     seeds[s].Eid = P(oEid[s]);
     seeds[s].node_begin = h->site_begin[s];
     seeds[s].node_end = h->site_begin[s + 1];
@@ -669,16 +684,18 @@ static mps_status build_energy_cache(const Layout& L, const StateBuf& sb, mps_ha
   ec.d_ob_off = reinterpret_cast<size_t*>(tbase + t_ob);
   ec.key_B = sb.B;
   ec.key_dims = sb.dims;
+  ec.key_Bbar = d_Bbar;
   return MPS_OK;
 }
 
 // Energy (and, when d_Bbar != null, the cotangent dE/dB* written in the state's site layout).
 static mps_status energy_pass_impl(const Layout& L, const StateBuf& sb, cudaStream_t st, int* status,
                                    mps_hamiltonian_dev* h, double* d_E, double* d_expect, double2* d_Bbar) {
-  if (!h->cache || h->cache->key_B != sb.B || h->cache->key_dims != sb.dims) {
+  if (!h->cache || h->cache->key_B != sb.B || h->cache->key_dims != sb.dims ||
+      (d_Bbar && h->cache->key_Bbar != d_Bbar)) {
     MPS_CU(cudaStreamSynchronize(st));
     h->cache.reset(new EnergyCache());
-    MPS_TRY(build_energy_cache(L, sb, h, *h->cache));
+    MPS_TRY(build_energy_cache(L, sb, h, d_Bbar, *h->cache));
   }
   EnergyCache& ec = *h->cache;
   const int nt = (int)h->x.size();
@@ -699,21 +716,9 @@ static mps_status energy_pass_impl(const Layout& L, const StateBuf& sb, cudaStre
         case Step::RSUM:
           launch_rsum(ec.Rsum[s.slot], ec.AR[s.slot], ec.RI[s.slot], h->c0, d_E, sb.dims, s.slot, s.max_m, st);
           break;
-        case Step::SEED: {
-          std::vector<SeedSite> seeds(L.n);
-          MPS_CU(cudaMemcpyAsync(seeds.data(), ec.d_seed, L.n * sizeof(SeedSite), cudaMemcpyDeviceToHost, st));
-          MPS_CU(cudaStreamSynchronize(st));
-          bool patch = false;
-          for (int q = 0; q < L.n; ++q)
-            if (seeds[q].out != d_Bbar + L.site_off[q]) {
-              seeds[q].out = d_Bbar + L.site_off[q];
-              patch = true;
-            }
-          if (patch)
-            MPS_CU(cudaMemcpyAsync(ec.d_seed, seeds.data(), L.n * sizeof(SeedSite), cudaMemcpyHostToDevice, st));
+        case Step::SEED:
           launch_seed_assemble(ec.d_seed, L.n, ec.d_Enode, ec.d_nodeop, sb.dims, ec.Z, ec.max_site, st);
           break;
-        }
       }
     }
     MPS_CU(cudaGetLastError());
@@ -853,8 +858,9 @@ static mps_status stage_theta(mps_state* s, const double* theta, int n_theta, co
     *d_theta = w.theta.as<double>();
     return MPS_OK;
   }
-  if (is_device_ptr(theta)) {
-    *d_theta = theta;   // finiteness is checked by the gate-matrix kernel
+  if (is_device_ptr(theta)) {   // finiteness is checked by the gate-matrix kernel
+    MPS_CU(cudaMemcpyAsync(w.theta.p, theta, n_theta * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
+    *d_theta = w.theta.as<double>();
     return MPS_OK;
   }
   for (int i = 0; i < n_theta; ++i)
@@ -871,12 +877,22 @@ static mps_status put_out(double* dst, const double* dsrc, size_t count, cudaStr
   return MPS_OK;
 }
 
-static mps_status gate_matrices(mps_state* s, const mps_circuit* c, const double* d_theta, int n_theta) {
+static mps_status ensure_gate_matrices(mps_state* s, const mps_circuit* c) {
   Workspace& w = *s->ws;
   MPS_TRY(w.G.ensure(std::max(1, c->n_gates) * 16 * sizeof(double2)));
   MPS_TRY(w.dG.ensure(std::max(1, c->n_gates) * 16 * sizeof(double2)));
+  return MPS_OK;
+}
+
+static void gate_matrices_launch(mps_state* s, const mps_circuit* c, const double* d_theta, int n_theta) {
+  Workspace& w = *s->ws;
   launch_gate_matrices(c->gates.p, c->n_gates, d_theta, n_theta, w.G.as<double2>(), w.dG.as<double2>(),
                        s->status.as<int>(), s->st);
+}
+
+static mps_status gate_matrices(mps_state* s, const mps_circuit* c, const double* d_theta, int n_theta) {
+  MPS_TRY(ensure_gate_matrices(s, c));
+  gate_matrices_launch(s, c, d_theta, n_theta);
   return MPS_OK;
 }
 
@@ -948,25 +964,27 @@ mps_status mps_profile(mps_state* s, int32_t enable) {
   clear_error();
   if (!s) return fail(MPS_EINVAL, "mps_profile: state is NULL");
   Workspace& w = *s->ws;
-  MPS_TRY(w.stats.ensure(2 * sizeof(double)));
+  MPS_TRY(w.stats.ensure(4 * sizeof(double)));
   w.profile = enable != 0;
   return MPS_OK;
 }
 
-mps_status mps_profile_read(mps_state* s, double* out4) {
+mps_status mps_profile_read(mps_state* s, double* out6) {
   clear_error();
-  if (!s || !out4) return fail(MPS_EINVAL, "mps_profile_read: NULL argument");
+  if (!s || !out6) return fail(MPS_EINVAL, "mps_profile_read: NULL argument");
   Workspace& w = *s->ws;
-  double fl[2] = {0.0, 0.0};
+  double fl[4] = {0.0, 0.0, 0.0, 0.0};
   if (w.stats.p) {
     MPS_CU(cudaStreamSynchronize(s->st));
     MPS_CU(cudaMemcpy(fl, w.stats.p, sizeof(fl), cudaMemcpyDeviceToHost));
     MPS_CU(cudaMemset(w.stats.p, 0, sizeof(fl)));
   }
-  out4[0] = w.svd_ms;
-  out4[1] = (double)w.svd_launches;
-  out4[2] = fl[0];
-  out4[3] = fl[1];
+  out6[0] = w.svd_ms;
+  out6[1] = (double)w.svd_launches;
+  out6[2] = fl[0];
+  out6[3] = fl[1];
+  out6[4] = fl[2] * 1e-6;
+  out6[5] = fl[3];
   w.svd_ms = 0.0;
   w.svd_launches = 0;
   return MPS_OK;
@@ -1011,6 +1029,7 @@ mps_status mps_circuit_create(int32_t n_qubits, const mps_gate* gates, int32_t n
   if (n_qubits < 2 || n_qubits > 64) return fail(MPS_EINVAL, "mps_circuit_create: n_qubits must be in 2..64");
   if (n_gates < 0 || (n_gates > 0 && !gates)) return fail(MPS_EINVAL, "mps_circuit_create: bad gate array");
   std::unique_ptr<mps_circuit> c(new mps_circuit());
+  c->uid = next_uid();
   c->n = n_qubits;
   c->n_gates = n_gates;
   c->host.assign(gates, gates + n_gates);
@@ -1064,6 +1083,7 @@ mps_status mps_hamiltonian_create(int32_t n_qubits, const mps_hamiltonian* hin, 
   if (hin->n_terms < 0 || (hin->n_terms > 0 && (!hin->x_mask || !hin->z_mask || !hin->coeff)))
     return fail(MPS_EINVAL, "mps_hamiltonian_create: bad term arrays");
   std::unique_ptr<mps_hamiltonian_dev> h(new mps_hamiltonian_dev());
+  h->uid = next_uid();
   h->n = n_qubits;
   const uint64_t valid = n_qubits == 64 ? ~0ull : ((1ull << n_qubits) - 1ull);
   struct T {
@@ -1286,7 +1306,8 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
   const double* d_theta = nullptr;
   MPS_TRY(stage_theta(s, theta, n_theta, &d_theta));
   MPS_TRY(ensure_forward_scratch(L, w));
-  MPS_TRY(gate_matrices(s, c, d_theta, n_theta));
+  MPS_TRY(ensure_gate_matrices(s, c));
+  MPS_TRY(w.stats.ensure(4 * sizeof(double)));
   w.ev_used = 0;
   const int ng = c->n_gates;
   // tape slot of one gate: pre-gate tensors, C, W, V, s, lambda_left, dims
@@ -1351,6 +1372,7 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
   Ctx cx{&L, &s->cfg, s->st, s->status.as<int>(), &w};
   const double2* G = w.G.as<double2>();
   const double2* dG = w.dG.as<double2>();
+  double* dE = w.scalars.as<double>();
   std::vector<TapeSlot> tapes;
   auto layout_tapes = [&](int g0, int g1) {
     tapes.assign(g1 - g0, TapeSlot{});
@@ -1376,41 +1398,88 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
       p += align256(db * sizeof(double));
     }
   };
-  double* dE = w.scalars.as<double>();
-  MPS_TRY(w.work.copy_from(s->buf, L, s->st));
-  if (nseg == 1) {
-    // whole-circuit tape: one forward pass records everything the reverse pass needs
-    layout_tapes(0, ng);
-    MPS_TRY(forward_gates(cx, w.work, c, G, 0, ng, &tapes));
+  // Everything from the gate matrices to dE/dtheta, enqueued on the state's stream with no host
+  // round trip, so that it can be captured once as a CUDA graph and replayed.
+  auto body = [&]() -> mps_status {
+    gate_matrices_launch(s, c, d_theta, n_theta);
+    MPS_TRY(w.work.copy_from(s->buf, L, s->st));
+    if (nseg == 1) {
+      // whole-circuit tape: one forward pass records everything the reverse pass needs
+      layout_tapes(0, ng);
+      MPS_TRY(forward_gates(cx, w.work, c, G, 0, ng, &tapes));
+    } else {
+      // forward with an MPS snapshot at the start of every segment
+      for (int seg = 0; seg < nseg; ++seg) {
+        MPS_TRY(w.snaps[seg]->copy_from(w.work, L, s->st));
+        MPS_TRY(forward_gates(cx, w.work, c, G, seg * K, std::min(ng, (seg + 1) * K), nullptr));
+      }
+    }
+    // energy and its cotangent
+    MPS_TRY(energy_pass_impl(L, w.work, s->st, s->status.as<int>(), h, dE, nullptr, w.Bbar.as<double2>()));
+    MPS_CU(cudaMemsetAsync(w.lambar.p, 0, L.lam_elems() * sizeof(double), s->st));
+    MPS_CU(cudaMemsetAsync(w.gate_grad.p, 0, std::max(1, ng) * sizeof(double), s->st));
+    // reverse, segment by segment (re-running a segment's forward from its snapshot with a tape)
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+      const int g0 = seg * K, g1 = std::min(ng, (seg + 1) * K);
+      if (nseg > 1) {
+        layout_tapes(g0, g1);
+        MPS_TRY(w.rec.copy_from(*w.snaps[seg], L, s->st));
+        MPS_TRY(forward_gates(cx, w.rec, c, G, g0, g1, &tapes));
+      }
+      for (int t = g1 - 1; t >= g0; --t)
+        MPS_TRY(reverse_gate(cx, t, c->host[t].bond, tapes[t - g0], w.Bbar.as<double2>(), w.lambar.as<double>(), G,
+                             dG, w.gate_grad.as<double>()));
+      MPS_CU(cudaGetLastError());
+    }
+    if (n_theta > 0) {
+      MPS_CU(cudaMemsetAsync(w.grad.p, 0, n_theta * sizeof(double), s->st));
+      launch_theta_reduce(w.gate_grad.as<double>(), c->csr_off.as<int>(), c->csr_gate.as<int>(),
+                          c->csr_scale.as<double>(), c->max_theta_idx + 1, w.grad.as<double>(), s->st);
+    }
+    return MPS_OK;
+  };
+  // The graph is valid while none of the buffers it touches has moved.
+  const EnergyCache* ec = h->cache.get();
+  std::vector<const void*> key = {(const void*)c->uid, (const void*)h->uid, (const void*)(intptr_t)n_theta,
+                                  (const void*)(intptr_t)K, w.tape.p, w.rv.p, w.Bbar.p, w.lambar.p,
+                                  w.gate_grad.p, w.grad.p, w.theta.p, w.G.p, w.dG.p, w.A.p, w.svd.p, w.C.p,
+                                  w.Vs.p, w.s.p, w.stats.p, w.scalars.p, w.work.mem.p, w.rec.mem.p,
+                                  ec, ec ? ec->bufs.p : nullptr, ec ? ec->tables.p : nullptr,
+                                  (const void*)(intptr_t)w.profile};
+  for (auto& sp : w.snaps) key.push_back(sp->mem.p);
+  if (w.graph_exec && key == w.graph_key) {
+    MPS_CU(cudaGraphLaunch(w.graph_exec, s->st));
+    add_launches(w.graph_kernels);
+  } else if (!w.profile && key == w.graph_seen && s->cfg.cuda_stream != nullptr) {
+    // second call with the same buffers: capture the call as a graph, then replay it
+    if (w.graph_exec) {
+      cudaGraphExecDestroy(w.graph_exec);
+      w.graph_exec = nullptr;
+    }
+    const long long l0 = mpsk::thread_launches();
+    MPS_CU(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+    mps_status st = body();
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(s->st, &graph);
+    if (st != MPS_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ce != cudaSuccess) return fail(MPS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&w.graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      w.graph_exec = nullptr;
+      return fail(MPS_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+    }
+    w.graph_kernels = mpsk::thread_launches() - l0;
+    mpsk::add_launches(-w.graph_kernels);   // captured, not launched: counted at each replay
+    w.graph_key = key;
+    MPS_CU(cudaGraphLaunch(w.graph_exec, s->st));
+    add_launches(w.graph_kernels);
   } else {
-    // forward with an MPS snapshot at the start of every segment
-    for (int seg = 0; seg < nseg; ++seg) {
-      MPS_TRY(w.snaps[seg]->copy_from(w.work, L, s->st));
-      MPS_TRY(forward_gates(cx, w.work, c, G, seg * K, std::min(ng, (seg + 1) * K), nullptr));
-    }
-  }
-  // energy and its cotangent
-  MPS_TRY(energy_pass_impl(L, w.work, s->st, s->status.as<int>(), h, dE, nullptr, w.Bbar.as<double2>()));
-  MPS_CU(cudaMemsetAsync(w.lambar.p, 0, L.lam_elems() * sizeof(double), s->st));
-  MPS_CU(cudaMemsetAsync(w.gate_grad.p, 0, std::max(1, ng) * sizeof(double), s->st));
-  // reverse, segment by segment (re-running a segment's forward from its snapshot with a tape)
-  for (int seg = nseg - 1; seg >= 0; --seg) {
-    const int g0 = seg * K, g1 = std::min(ng, (seg + 1) * K);
-    if (nseg > 1) {
-      layout_tapes(g0, g1);
-      MPS_TRY(w.rec.copy_from(*w.snaps[seg], L, s->st));
-      MPS_TRY(forward_gates(cx, w.rec, c, G, g0, g1, &tapes));
-    }
-    for (int t = g1 - 1; t >= g0; --t)
-      MPS_TRY(reverse_gate(cx, t, c->host[t].bond, tapes[t - g0], w.Bbar.as<double2>(), w.lambar.as<double>(), G, dG,
-                           w.gate_grad.as<double>()));
-    MPS_CU(cudaGetLastError());
-  }
-  const int nth_c = c->max_theta_idx + 1;
-  if (n_theta > 0) {
-    MPS_CU(cudaMemsetAsync(w.grad.p, 0, n_theta * sizeof(double), s->st));
-    launch_theta_reduce(w.gate_grad.as<double>(), c->csr_off.as<int>(), c->csr_gate.as<int>(),
-                        c->csr_scale.as<double>(), nth_c, w.grad.as<double>(), s->st);
+    MPS_TRY(body());
+    w.graph_seen = key;
   }
   MPS_TRY(put_out(E_out, dE, 1, s->st));
   MPS_TRY(put_out(grad_out, w.grad.as<double>(), n_theta, s->st));

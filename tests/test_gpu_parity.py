@@ -232,3 +232,24 @@ def test_energy_cotangent_matches_oracle(M, case):
     assert abs(E - Eo) <= E_TOL * max(1.0, abs(Eo))
     scale = max(np.abs(b).max() for b in Bo)
     assert max(np.abs(a - b).max() for a, b in zip(Bbar, Bo)) <= 1e-11 * scale
+
+
+def test_graph_replay_is_bit_identical(M):
+    """Calls 1 (eager), 2 (captured as a CUDA graph) and 3 (replayed) give the same bits."""
+    import torch
+    p = S.make_problem(1)
+    excs = p.excitations[:15]
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    stream = torch.cuda.Stream()
+    st = M.State.product(p.bits, p.spec.D, p.spec.eps, stream=stream)
+    circ = M.Circuit(p.n, M.compile_excitations(p.n, excs))
+    ham = M.Hamiltonian(p.n, x, z, c)
+    th = p.theta[: len(excs)]
+    res = [M.energy_grad(st, circ, th, ham) for _ in range(3)]
+    th2 = th + 0.1                                   # new angles through the same graph
+    E2, g2 = M.energy_grad(st, circ, th2, ham)
+    for E, g in res[1:]:
+        assert E == res[0][0] and np.array_equal(g, res[0][1])
+    st_eager = M.State.product(p.bits, p.spec.D, p.spec.eps)          # default stream: never captured
+    E2e, g2e = M.energy_grad(st_eager, circ, th2, ham)
+    assert E2 == E2e and np.array_equal(g2, g2e)
