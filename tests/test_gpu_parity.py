@@ -253,3 +253,34 @@ def test_graph_replay_is_bit_identical(M):
     st_eager = M.State.product(p.bits, p.spec.D, p.spec.eps)          # default stream: never captured
     E2e, g2e = M.energy_grad(st_eager, circ, th2, ham)
     assert E2 == E2e and np.array_equal(g2, g2e)
+
+
+def test_autograd_function_backward_is_the_library_gradient(M):
+    import torch
+    from paper_2211_07983_gb300.autograd import mps_energy
+    p = S.make_problem(0)
+    st, circ, ham, th = prepare(M, p)
+    theta = torch.tensor(th, dtype=torch.float64, device="cuda", requires_grad=True)
+    E = mps_energy(theta, st, circ, ham)
+    (3.0 * E).backward()
+    E_ref, g_ref = M.energy_grad(st, circ, th, ham)
+    assert abs(E.item() - E_ref) < 1e-14
+    assert np.abs(theta.grad.cpu().numpy() - 3.0 * g_ref).max() < 1e-13
+
+
+def test_string_shards_sum_to_the_full_cotangent_on_gpu(M):
+    """The sharded-energy identity of parallel.py, computed by the library on one GPU."""
+    from paper_2211_07983_gb300 import parallel
+    p = S.make_problem(1)
+    excs = p.excitations[:20]
+    st, circ, ham, th = prepare(M, p, excs)
+    M.apply_circuit(st, circ, th)
+    E, Bbar = M.energy_cotangent(st, ham)
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    E_sum, B_sum = 0.0, None
+    for idx in parallel.shard_terms(x, z, c, 3):
+        Er, Br = M.energy_cotangent(st, M.Hamiltonian(p.n, x[idx], z[idx], c[idx]))
+        E_sum += Er
+        B_sum = Br if B_sum is None else [a + b for a, b in zip(B_sum, Br)]
+    assert abs(E_sum - E) < 1e-12
+    assert max(np.abs(a - b).max() for a, b in zip(B_sum, Bbar)) < 1e-12
