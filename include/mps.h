@@ -213,6 +213,25 @@ mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, doub
                        double* V_out, double* W_out, int32_t* k_out);
 
 /*
+ * The gate SVD of mps_svd_dev without any memory allocation, for callers that cannot allocate
+ * device memory: code that runs while a CUDA graph is being captured (cudaMalloc cannot be
+ * captured), code in latency-critical loops where the implicit device synchronisation of
+ * cudaMalloc/cudaFree is not acceptable, and embedders whose device memory is owned by another
+ * allocator.  The paper has no counterpart; this is a service of the library.
+ *   m, ncol: even, 2..128 (larger sizes are rejected with MPS_EINVAL: the scratch is fixed).
+ *   A, s_out, V_out, W_out, k_out: device memory owned by the caller, same layouts and meaning
+ *   as in mps_svd_dev (K = min(m, ncol)).  cuda_stream: cudaStream_t or NULL.
+ * Scratch: one file-scope device array of about 1.25 MiB inside the library, held by every GPU
+ * that loads the library until the process exits.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls on a device share the array, which keeps the last
+ * call's contents: calls that overlap on the GPU (different streams or threads) race and must
+ * be serialised by the caller.  The call synchronises `cuda_stream` to read the status word.
+ */
+mps_status mps_svd_noalloc(int32_t m, int32_t ncol, const double* A, int32_t D, double eps, double* s_out,
+                           double* V_out, double* W_out, int32_t* k_out, void* cuda_stream);
+
+/*
  * Profiling of the gate SVD, the dominant kernel.  While enabled, every SVD launch of calls on
  * this state is bracketed by CUDA events on the state's stream and the SVD kernel adds the
  * floating-point operations its sweeps actually performed to a device counter.
