@@ -19,6 +19,14 @@
  * synchronises that stream before returning, because it reads the device status
  * word; outputs may still be device pointers (no host round trip of the data).
  *
+ * Instances: a state may hold n_inst >= 1 independent instances of the same qubit count
+ * and configuration (mps_init_product_batch), e.g. the points of a batched VQE step.  Every
+ * kernel of a call then runs over all instances at once.  For such a state, every per-call
+ * array below holds one row per instance, instance-major: theta is n_inst x n_theta, E_out
+ * n_inst values, grad_out n_inst x n_theta, gate_grad_out n_inst x n_gates, expect_out
+ * n_inst x (strings).  With n_inst = 1 (mps_init_product) these are the plain shapes.  A
+ * device-side error reports the first failing instance in mps_last_error().
+ *
  * Notation (Sec. 3): n qubits = n sites; site tensor B_s[Dl][2][Dr], row-major,
  * Dr fastest; bond b joins sites b and b+1 and carries the Schmidt vector
  * lambda_b; bond dimensions never exceed min(2^(b+1), 2^(n-b-1), max_bond).
@@ -132,7 +140,19 @@ mps_status mps_compile_excitations(int32_t n, const int32_t* exc, int32_t n_exc,
 mps_status mps_init_product(int32_t n_qubits, const uint8_t* bits, const mps_config* cfg,
                             mps_state** out);
 
-/* Deep copy of a state (same config and stream). */
+/*
+ * n_inst product states in one state object (1 <= n_inst <= 4096).  bits: host, n_inst x
+ * n_qubits bytes of 0/1 (row r is instance r).  The instances are replicas of one device
+ * address layout (driver virtual-memory mappings, grown on demand), so one kernel launch
+ * serves all of them; each instance's memory is committed only as it is used.
+ */
+mps_status mps_init_product_batch(int32_t n_inst, int32_t n_qubits, const uint8_t* bits,
+                                  const mps_config* cfg, mps_state** out);
+
+/* Number of instances of a state. */
+mps_status mps_state_instances(const mps_state* s, int32_t* n_inst);
+
+/* Deep copy of a state (same config, stream and instance count). */
 mps_status mps_clone(const mps_state* s, mps_state** out);
 
 /* Copy a state back to the host.  dims: n+1 ints (bond dims, dims[0] = dims[n] = 1);
@@ -140,6 +160,9 @@ mps_status mps_clone(const mps_state* s, mps_state** out);
  * tensors: sum_s dims[s]*2*dims[s+1] complex values as interleaved doubles,
  * sites in order, each [Dl][2][Dr] row-major, or NULL. */
 mps_status mps_read_state(const mps_state* s, int32_t* dims, double* lam, double* tensors);
+/* The same for instance `inst` (0 <= inst < n_inst); mps_read_state reads instance 0. */
+mps_status mps_read_state_instance(const mps_state* s, int32_t inst, int32_t* dims, double* lam,
+                                   double* tensors);
 
 /* Upload a gate list once (validated: bonds in range, finite matrices). */
 mps_status mps_circuit_create(int32_t n_qubits, const mps_gate* gates, int32_t n_gates,
@@ -178,7 +201,8 @@ mps_status mps_energy_dev(const mps_state* s, const mps_hamiltonian_dev* h, doub
  * [sum_k c_k env_k(s) - E env_I(s)] / <psi|psi> with env_P(s) the network of
  * <psi|P|psi> with conj(B_s) removed (Sec. 4, Eq. expecgrad: dE/d<psi| = H|psi>
  * normalised).  Bbar_out: host or device, complex values as interleaved doubles in the
- * layout of mps_read_state's `tensors` (current bond dims).
+ * layout of mps_read_state's `tensors` (current bond dims), of instance 0; E_out: one value
+ * per instance.
  */
 mps_status mps_energy_cotangent_dev(const mps_state* s, const mps_hamiltonian_dev* h, double* E_out,
                                     double* Bbar_out);

@@ -55,6 +55,9 @@ _SIGS = {
                                         P(c_double), P(c_int64)]),
     "mps_compile_excitations": (c_int32, [c_int32, P(c_int32), c_int32, c_int64, c_void_p, P(c_int64)]),
     "mps_init_product": (c_int32, [c_int32, P(c_uint8), P(MpsConfig), P(c_void_p)]),
+    "mps_init_product_batch": (c_int32, [c_int32, c_int32, P(c_uint8), P(MpsConfig), P(c_void_p)]),
+    "mps_state_instances": (c_int32, [c_void_p, P(c_int32)]),
+    "mps_read_state_instance": (c_int32, [c_void_p, c_int32, P(c_int32), P(c_double), P(c_double)]),
     "mps_clone": (c_int32, [c_void_p, P(c_void_p)]),
     "mps_read_state": (c_int32, [c_void_p, P(c_int32), P(c_double), P(c_double)]),
     "mps_circuit_create": (c_int32, [c_int32, c_void_p, c_int32, P(c_void_p)]),

@@ -88,11 +88,16 @@ def compile_excitations(n: int, excitations) -> np.ndarray:
 # ---- handles --------------------------------------------------------------------------------
 
 class State:
-    """mps_state: an MPS resident on the GPU (mps_init_product / mps_clone / mps_free)."""
+    """mps_state: an MPS resident on the GPU (mps_init_product[_batch] / mps_clone / mps_free).
 
-    def __init__(self, handle, n):
+    A state may hold n_inst instances (product_batch); per-call arrays then carry one row per
+    instance (theta [n_inst, n_theta], E [n_inst], grad [n_inst, n_theta]).
+    """
+
+    def __init__(self, handle, n, n_inst=1):
         self._h = handle
         self.n = n
+        self.n_inst = n_inst
 
     @classmethod
     def product(cls, bits, max_bond: int, cutoff: float, checkpoint_every: int = 0, stream=None):
@@ -104,22 +109,34 @@ class State:
                                    ctypes.byref(h)))
         return cls(h, len(bits))
 
+    @classmethod
+    def product_batch(cls, bits_rows, max_bond: int, cutoff: float, checkpoint_every: int = 0, stream=None):
+        """mps_init_product_batch: one product state per row of `bits_rows` ([n_inst, n])."""
+        lib = _lib.load()
+        bits = np.ascontiguousarray(np.atleast_2d(bits_rows), dtype=np.uint8)
+        cfg = MpsConfig(max_bond, cutoff, _lib.PRECISION_FP64, checkpoint_every, _stream_handle(stream))
+        h = ctypes.c_void_p()
+        check(lib.mps_init_product_batch(bits.shape[0], bits.shape[1], bits.ctypes.data_as(P(ctypes.c_uint8)),
+                                         ctypes.byref(cfg), ctypes.byref(h)))
+        return cls(h, bits.shape[1], bits.shape[0])
+
     def clone(self):
         h = ctypes.c_void_p()
         check(_lib.load().mps_clone(self._h, ctypes.byref(h)))
-        return State(h, self.n)
+        return State(h, self.n, self.n_inst)
 
-    def read(self):
-        """(dims, lambdas per bond, site tensors) copied to the host."""
+    def read(self, inst: int = 0):
+        """(dims, lambdas per bond, site tensors) of one instance, copied to the host."""
         lib = _lib.load()
         dims = np.zeros(self.n + 1, dtype=np.int32)
-        check(lib.mps_read_state(self._h, dims.ctypes.data_as(P(ctypes.c_int32)), None, None))
+        check(lib.mps_read_state_instance(self._h, inst, dims.ctypes.data_as(P(ctypes.c_int32)), None, None))
         nl = int(dims[1:-1].sum())
         ne = int(sum(dims[s] * 2 * dims[s + 1] for s in range(self.n)))
         lam = np.zeros(max(nl, 1))
         ten = np.zeros(2 * max(ne, 1))
-        check(lib.mps_read_state(self._h, dims.ctypes.data_as(P(ctypes.c_int32)),
-                                 lam.ctypes.data_as(P(ctypes.c_double)), ten.ctypes.data_as(P(ctypes.c_double))))
+        check(lib.mps_read_state_instance(self._h, inst, dims.ctypes.data_as(P(ctypes.c_int32)),
+                                          lam.ctypes.data_as(P(ctypes.c_double)),
+                                          ten.ctypes.data_as(P(ctypes.c_double))))
         lams, o = [], 0
         for b in range(1, self.n):
             lams.append(lam[o:o + dims[b]].copy())
@@ -204,25 +221,37 @@ class Hamiltonian:
 
 # ---- steps S1-S9 ----------------------------------------------------------------------------
 
+def _n_theta(state: State, theta) -> int:
+    shape = tuple(theta.shape)
+    if state.n_inst == 1 and len(shape) == 1:
+        return shape[0]
+    if len(shape) != 2 or shape[0] != state.n_inst:
+        raise ValueError(f"theta must have shape [{state.n_inst}, n_theta] for this state")
+    return shape[1]
+
+
 def apply_circuit(state: State, circuit: Circuit, theta) -> None:
-    """mps_apply_circuit_dev: |state> <- U(theta)|state>."""
+    """mps_apply_circuit_dev: |state> <- U(theta)|state> (theta: [n_theta] or [n_inst, n_theta])."""
     theta = _f64(theta)
-    check(_lib.load().mps_apply_circuit_dev(state._h, circuit._h, _ptr(theta), len(theta)))
+    check(_lib.load().mps_apply_circuit_dev(state._h, circuit._h, _ptr(theta), _n_theta(state, theta)))
 
 
 def energy(state: State, ham: Hamiltonian, expect=False):
     """mps_energy_dev: E (and optionally Re<P_k>/<psi|psi> in canonical order)."""
-    E = np.zeros(1)
-    ex = np.zeros(ham.n_terms) if expect else None
+    ni = state.n_inst
+    E = np.zeros(ni)
+    ex = np.zeros((ni, ham.n_terms)) if expect else None
     check(_lib.load().mps_energy_dev(state._h, ham._h, _ptr(E), _ptr(ex)))
-    return (float(E[0]), ex) if expect else float(E[0])
+    if ni == 1:
+        return (float(E[0]), ex[0]) if expect else float(E[0])
+    return (E, ex) if expect else E
 
 
 def energy_cotangent(state: State, ham: Hamiltonian):
     """mps_energy_cotangent_dev: E and dE/dB_s* per site (list of [Dl, 2, Dr] arrays)."""
     dims, _, _ = state.read()
     ne = int(sum(dims[s] * 2 * dims[s + 1] for s in range(state.n)))
-    E = np.zeros(1)
+    E = np.zeros(state.n_inst)
     buf = np.zeros(2 * max(ne, 1))
     check(_lib.load().mps_energy_cotangent_dev(state._h, ham._h, _ptr(E), _ptr(buf)))
     cplx = buf[: 2 * ne].view(np.complex128)
@@ -237,19 +266,23 @@ def energy_cotangent(state: State, ham: Hamiltonian):
 def energy_grad(state0: State, circuit: Circuit, theta, ham: Hamiltonian, out=None, gate_grad=False):
     """mps_energy_grad_dev: E(theta), dE/dtheta (and dE/dphi per gate) of U(theta)|state0>.
 
+    theta: [n_theta], or [n_inst, n_theta] for a batched state (E [n_inst], grad [n_inst, n_theta]).
     `out`: optional (E, grad) arrays/tensors receiving the results (may be CUDA tensors).
     """
     theta = _f64(theta)
+    nth = _n_theta(state0, theta)
+    ni = state0.n_inst
     if out is None:
-        E_out, g_out = np.zeros(1), np.zeros(len(theta))
+        E_out, g_out = np.zeros(ni), np.zeros((ni, nth) if ni > 1 else nth)
     else:
         E_out, g_out = out
-    gg = np.zeros(circuit.n_gates) if gate_grad else None
-    check(_lib.load().mps_energy_grad_dev(state0._h, circuit._h, _ptr(theta), len(theta), ham._h, _ptr(E_out),
+    gg = (np.zeros((ni, circuit.n_gates) if ni > 1 else circuit.n_gates)) if gate_grad else None
+    check(_lib.load().mps_energy_grad_dev(state0._h, circuit._h, _ptr(theta), nth, ham._h, _ptr(E_out),
                                           _ptr(g_out), _ptr(gg)))
     if out is not None:
         return out
-    return (float(E_out[0]), g_out, gg) if gate_grad else (float(E_out[0]), g_out)
+    E = float(E_out[0]) if ni == 1 else E_out
+    return (E, g_out, gg) if gate_grad else (E, g_out)
 
 
 def svd(A: np.ndarray, D: int, eps: float):

@@ -28,6 +28,23 @@ __host__ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c
   return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
 
+// ---- instance batching ------------------------------------------------------------------------
+// A state may hold n instances (independent evaluations of the same circuit shape).  They are
+// replicas of one address layout, `stride` bytes apart: instance i's copy of any per-instance
+// byte sits i*stride bytes after instance 0's.  Every kernel takes its instance from one grid
+// dimension and shifts each per-instance pointer by i*stride, both its arguments and the
+// pointers it reads from descriptor tables.  Shared read-only tables (the gate list, Hamiltonian
+// coefficients, offset tables, the descriptor tables themselves) are not shifted.
+struct Batch {
+  int n;           // instances per launch
+  size_t stride;   // bytes between instances
+};
+
+template <class T>
+__host__ __device__ __forceinline__ T* ish(T* p, size_t off) {
+  return p ? reinterpret_cast<T*>(reinterpret_cast<uintptr_t>(p) + off) : p;
+}
+
 // ---- device status word -----------------------------------------------------------------
 // First error wins; the host reads it after the stream work of a call completes.
 __device__ __forceinline__ void set_status(int* status, int code) {

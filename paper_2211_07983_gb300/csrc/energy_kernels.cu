@@ -21,8 +21,12 @@ __device__ __forceinline__ double warp_sum(double v) {
 // conj(O B) (Pauli matrices are Hermitian).
 __global__ void apply_paulis_kernel(const double2* __restrict__ B, const size_t* __restrict__ site_off,
                                     const size_t* __restrict__ ob_off, const int* __restrict__ dims,
-                                    double2* OB) {
-  const int s = blockIdx.y, o = blockIdx.z;
+                                    double2* OB, int n, size_t stride) {
+  const int inst = blockIdx.y / n, s = blockIdx.y - inst * n, o = blockIdx.z;
+  const size_t io = (size_t)inst * stride;
+  B = ish(B, io);
+  dims = ish(dims, io);
+  OB = ish(OB, io);
   const int Dl = dims[s], Dr = dims[s + 1];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= Dl * Dr) return;
@@ -47,13 +51,16 @@ __global__ void apply_paulis_kernel(const double2* __restrict__ B, const size_t*
 
 __global__ void env_dots_kernel(const double2* const* __restrict__ Ls, const double2* const* __restrict__ Rs,
                                 const int* __restrict__ didx, const int* __restrict__ dims, int count,
-                                double2* e) {
+                                double2* e, size_t stride) {
   const int t = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (t >= count) return;
+  const size_t io = (size_t)blockIdx.y * stride;
+  dims = ish(dims, io);
+  e = ish(e, io);
   const int D = dims[didx[t]];
-  const double2* L = Ls[t];
-  const double2* R = Rs[t];
+  const double2* L = ish(Ls[t], io);
+  const double2* R = ish(Rs[t], io);
   double re = 0.0, im = 0.0;
   for (int x = lane; x < D * D; x += 32) {
     const double2 l = L[x], r = R[x];
@@ -69,8 +76,14 @@ __global__ void env_dots_kernel(const double2* const* __restrict__ Ls, const dou
 // l, l+32, ...; the 32 partial (sum, compensation) pairs are then added by lane 0 in order.
 __global__ void energy_sum_kernel(const double2* __restrict__ e, const double* __restrict__ c, int n,
                                   double c0, const double2* __restrict__ Z, double* E_out, double* expect,
-                                  int* status) {
+                                  int* status, size_t stride) {
   const int lane = threadIdx.x;
+  const size_t io = (size_t)blockIdx.x * stride;
+  e = ish(e, io);
+  Z = ish(Z, io);
+  E_out = ish(E_out, io);
+  expect = ish(expect, io);
+  status = ish(status, io);
   const double z = Z->x;
   double sum = 0.0, comp = 0.0;
   for (int k = lane; k < n; k += 32) {
@@ -101,29 +114,37 @@ __global__ void energy_sum_kernel(const double2* __restrict__ e, const double* _
 }
 
 __global__ void axpy_lists_kernel(const AxpyList* __restrict__ lists, const double2* const* __restrict__ src,
-                                  const double* __restrict__ coef, const int* __restrict__ dims) {
+                                  const double* __restrict__ coef, const int* __restrict__ dims, size_t stride) {
   const AxpyList& L = lists[blockIdx.y];
+  const size_t io = (size_t)blockIdx.z * stride;
+  dims = ish(dims, io);
   const int D = dims[L.didx];
   const long long ne = (long long)D * D * L.mult;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ne) return;
-  double2 v = L.accumulate ? L.out[t] : make_double2(0.0, 0.0);
-  for (int j = L.src_begin; j < L.src_end; ++j) v = cadd(v, cscale(src[j][t], coef[j]));
-  L.out[t] = v;
+  double2* out = ish(L.out, io);
+  double2 v = L.accumulate ? out[t] : make_double2(0.0, 0.0);
+  for (int j = L.src_begin; j < L.src_end; ++j) v = cadd(v, cscale(ish(src[j], io)[t], coef[j]));
+  out[t] = v;
 }
 
 __global__ void seed_assemble_kernel(const SeedSite* __restrict__ sites, const double2* const* __restrict__ Enode,
                                      const int* __restrict__ node_op, const int* __restrict__ dims,
-                                     const double2* __restrict__ Z) {
+                                     const double2* __restrict__ Z, size_t stride) {
   const SeedSite& S = sites[blockIdx.y];
+  const size_t io = (size_t)blockIdx.z * stride;
+  dims = ish(dims, io);
+  Z = ish(Z, io);
   const int Dl = dims[S.s], Dr = dims[S.s + 1];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= Dl * Dr) return;
   const int a = t / Dr, c = t % Dr;
   const size_t i0 = (size_t)(2 * a) * Dr + c, i1 = (size_t)(2 * a + 1) * Dr + c;
-  double2 v0 = S.Eid[i0], v1 = S.Eid[i1];
+  const double2* Eid = ish(S.Eid, io);
+  double2 v0 = Eid[i0], v1 = Eid[i1];
   for (int nd = S.node_begin; nd < S.node_end; ++nd) {
-    const double2 e0 = Enode[nd][i0], e1 = Enode[nd][i1];
+    const double2* En = ish(Enode[nd], io);
+    const double2 e0 = En[i0], e1 = En[i1];
     const int o = node_op[nd];   // out[i'] += sum_i O[i', i] E[i]; 0 I, 1 X, 2 Y, 3 Z
     if (o == 0) {
       v0 = cadd(v0, e0);
@@ -140,12 +161,20 @@ __global__ void seed_assemble_kernel(const SeedSite* __restrict__ sites, const d
     }
   }
   const double iz = 1.0 / Z->x;
-  S.out[i0] = cscale(v0, iz);
-  S.out[i1] = cscale(v1, iz);
+  double2* out = ish(S.out, io);
+  out[i0] = cscale(v0, iz);
+  out[i1] = cscale(v1, iz);
 }
 
 __global__ void rsum_kernel(double2* out, const double2* __restrict__ AR, const double2* __restrict__ RI,
-                            double c0, const double* __restrict__ E, const int* __restrict__ dims, int slot) {
+                            double c0, const double* __restrict__ E, const int* __restrict__ dims, int slot,
+                            size_t stride) {
+  const size_t io = (size_t)blockIdx.y * stride;
+  out = ish(out, io);
+  AR = ish(AR, io);
+  RI = ish(RI, io);
+  E = ish(E, io);
+  dims = ish(dims, io);
   const int D = dims[slot];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= D * D) return;
@@ -154,45 +183,45 @@ __global__ void rsum_kernel(double2* out, const double2* __restrict__ AR, const 
 
 }  // namespace
 
-void launch_rsum(double2* out, const double2* AR, const double2* RI, double c0, const double* E, const int* dims,
-                 int slot, int max_elems, cudaStream_t st) {
-  rsum_kernel<<<cdiv(max_elems, 256), 256, 0, st>>>(out, AR, RI, c0, E, dims, slot);
+void launch_rsum(const Batch& bt, double2* out, const double2* AR, const double2* RI, double c0, const double* E,
+                 const int* dims, int slot, int max_elems, cudaStream_t st) {
+  rsum_kernel<<<dim3(cdiv(max_elems, 256), bt.n), 256, 0, st>>>(out, AR, RI, c0, E, dims, slot, bt.stride);
   note_launch();
 }
 
-void launch_apply_paulis(const double2* B, const size_t* site_off, const size_t* ob_off, const int* dims, int n,
-                         double2* OB, int max_site, cudaStream_t st) {
-  dim3 grid(cdiv(max_site, 128), n, 3);
-  apply_paulis_kernel<<<grid, 128, 0, st>>>(B, site_off, ob_off, dims, OB);
+void launch_apply_paulis(const Batch& bt, const double2* B, const size_t* site_off, const size_t* ob_off,
+                         const int* dims, int n, double2* OB, int max_site, cudaStream_t st) {
+  dim3 grid(cdiv(max_site, 128), n * bt.n, 3);
+  apply_paulis_kernel<<<grid, 128, 0, st>>>(B, site_off, ob_off, dims, OB, n, bt.stride);
   note_launch();
 }
 
-void launch_env_dots(const double2* const* Ls, const double2* const* Rs, const int* didx, const int* dims,
-                     int count, double2* e, cudaStream_t st) {
+void launch_env_dots(const Batch& bt, const double2* const* Ls, const double2* const* Rs, const int* didx,
+                     const int* dims, int count, double2* e, cudaStream_t st) {
   if (count <= 0) return;
-  env_dots_kernel<<<cdiv(count, 8), 256, 0, st>>>(Ls, Rs, didx, dims, count, e);
+  env_dots_kernel<<<dim3(cdiv(count, 8), bt.n), 256, 0, st>>>(Ls, Rs, didx, dims, count, e, bt.stride);
   note_launch();
 }
 
-void launch_energy_sum(const double2* e, const double* c, int n_terms, double c0, const double2* Z, double* E_out,
-                       double* expect, int* status, cudaStream_t st) {
-  energy_sum_kernel<<<1, 32, 0, st>>>(e, c, n_terms, c0, Z, E_out, expect, status);
+void launch_energy_sum(const Batch& bt, const double2* e, const double* c, int n_terms, double c0,
+                       const double2* Z, double* E_out, double* expect, int* status, cudaStream_t st) {
+  energy_sum_kernel<<<bt.n, 32, 0, st>>>(e, c, n_terms, c0, Z, E_out, expect, status, bt.stride);
   note_launch();
 }
 
-void launch_axpy_lists(const AxpyList* lists, int count, const double2* const* src, const double* src_coef,
-                       const int* dims, int max_elems, cudaStream_t st) {
+void launch_axpy_lists(const Batch& bt, const AxpyList* lists, int count, const double2* const* src,
+                       const double* src_coef, const int* dims, int max_elems, cudaStream_t st) {
   if (count <= 0 || max_elems <= 0) return;
-  dim3 grid(cdiv(max_elems, 256), count);
-  axpy_lists_kernel<<<grid, 256, 0, st>>>(lists, src, src_coef, dims);
+  dim3 grid(cdiv(max_elems, 256), count, bt.n);
+  axpy_lists_kernel<<<grid, 256, 0, st>>>(lists, src, src_coef, dims, bt.stride);
   note_launch();
 }
 
-void launch_seed_assemble(const SeedSite* sites, int n_sites, const double2* const* Enode, const int* node_op,
-                          const int* dims, const double2* Z, int max_site, cudaStream_t st) {
+void launch_seed_assemble(const Batch& bt, const SeedSite* sites, int n_sites, const double2* const* Enode,
+                          const int* node_op, const int* dims, const double2* Z, int max_site, cudaStream_t st) {
   if (n_sites <= 0) return;
-  dim3 grid(cdiv(max_site, 128), n_sites);
-  seed_assemble_kernel<<<grid, 128, 0, st>>>(sites, Enode, node_op, dims, Z);
+  dim3 grid(cdiv(max_site, 128), n_sites, bt.n);
+  seed_assemble_kernel<<<grid, 128, 0, st>>>(sites, Enode, node_op, dims, Z, bt.stride);
   note_launch();
 }
 

@@ -31,16 +31,49 @@ using mpsk::GemmDesc;
     if (s_ != MPS_OK) return s_;       \
   } while (0)
 
-// Owned device allocation.
+mps_status legacy_fence();
+
+// Device memory of a state's instances: n copies of one address layout, `stride` bytes apart
+// (instance i's copy of a byte at address a is at a + i*stride).  The layout grows on demand:
+// alloc() hands out a zero-filled range in every copy, mapping physical memory as needed.
+// Ranges are released only with the arena.
+struct Arena {
+  long long uid = 0;   // unique per arena (keys plans built against it)
+  int n = 1, dev = 0;
+  size_t stride = 0, gran = 0;
+  uintptr_t base = 0;
+  size_t used = 0, mapped = 0;   // per instance
+  struct Mapping {
+    uintptr_t at;
+    size_t bytes;
+    unsigned long long handle;
+  };
+  std::vector<Mapping> maps;
+  Arena() = default;
+  Arena(const Arena&) = delete;
+  Arena& operator=(const Arena&) = delete;
+  ~Arena();
+  mps_status init(int n_inst);
+  mps_status alloc(size_t nbytes, void** out);
+  mpsk::Batch batch() const { return mpsk::Batch{n, stride}; }
+
+ private:
+  mps_status grow(size_t need);
+};
+
+// Device allocation: owned (cudaMalloc) or, when `arena` is set, a per-instance range of that
+// arena (released with the arena).
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  Arena* arena = nullptr;
   DevBuf() = default;
+  explicit DevBuf(Arena* a) : arena(a) {}
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { reset(); }
   void reset() {
-    if (p) cudaFree(p);
+    if (p && !arena) cudaFree(p);
     p = nullptr;
     bytes = 0;
   }
@@ -63,12 +96,13 @@ struct Layout {
   size_t lam_elems() const { return lam_off[n + 1]; }
 };
 
-// Device storage of one MPS (tensors, Schmidt vectors, bond dims).
+// Device storage of one MPS (tensors, Schmidt vectors, bond dims), per instance.
 struct StateBuf {
   DevBuf mem;
   double2* B = nullptr;
   double* lam = nullptr;
   int* dims = nullptr;
+  explicit StateBuf(Arena* a = nullptr) : mem(a) {}
   mps_status alloc(const Layout& L);
   mps_status copy_from(const StateBuf& o, const Layout& L, cudaStream_t st);
 };
@@ -78,12 +112,16 @@ struct Workspace;
 }  // namespace mpsi
 
 struct mps_state {
+  long long uid = 0;     // unique per created state (keys the energy plan)
   mpsi::Layout L;
   mps_config cfg{};
   cudaStream_t st = nullptr;
+  std::unique_ptr<mpsi::Arena> arena;   // declared first: released after every buffer below
   mpsi::StateBuf buf;
-  mpsi::DevBuf status;   // one int
+  mpsi::DevBuf status;   // one int per instance
   std::unique_ptr<mpsi::Workspace> ws;
+  int n_inst() const { return arena->n; }
+  mpsk::Batch batch() const { return arena->batch(); }
 };
 
 struct mps_circuit {

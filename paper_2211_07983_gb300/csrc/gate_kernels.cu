@@ -19,9 +19,14 @@ struct GateView {
 
 __global__ void gate_matrices_kernel(const mps_gate* __restrict__ gates, int n_gates,
                                      const double* __restrict__ theta, int n_theta, double2* G, double2* dG,
-                                     int* status) {
+                                     int* status, size_t stride) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_gates) return;
+  const size_t io = (size_t)blockIdx.y * stride;
+  theta = ish(theta, io);
+  G = ish(G, io);
+  dG = ish(dG, io);
+  status = ish(status, io);
   const mps_gate& g = gates[t];
   GateView v{&g};
   if (g.theta_idx < 0) {
@@ -63,9 +68,25 @@ __global__ void gate_matrices_kernel(const mps_gate* __restrict__ gates, int n_g
 
 __global__ void contract_kernel(const double2* __restrict__ Bl, const double2* __restrict__ Br,
                                 const int* __restrict__ dims, int b, const double2* __restrict__ Gm,
-                                const double* __restrict__ lam_left, double2* C, double2* A) {
+                                const double* __restrict__ lam_left, double2* C, double2* A,
+                                double2* __restrict__ Bl_tape, double2* __restrict__ Br_tape, size_t stride) {
+  const size_t io = (size_t)blockIdx.y * stride;
+  Bl = ish(Bl, io);
+  Br = ish(Br, io);
+  dims = ish(dims, io);
+  Gm = ish(Gm, io);
+  lam_left = ish(lam_left, io);
+  C = ish(C, io);
+  A = ish(A, io);
+  Bl_tape = ish(Bl_tape, io);
+  Br_tape = ish(Br_tape, io);
   const int Dl = dims[b], Dm = dims[b + 1], Dr = dims[b + 2];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (Bl_tape) {   // tape copies of the two input tensors at their current (compact) sizes
+    const int nl = 2 * Dl * Dm, nr = 2 * Dm * Dr, stride = gridDim.x * blockDim.x;
+    for (int i = t; i < nl; i += stride) Bl_tape[i] = Bl[i];
+    for (int i = t; i < nr; i += stride) Br_tape[i] = Br[i];
+  }
   if (t >= Dl * Dr) return;
   const int a = t / Dr, c = t % Dr;
   const int m = 2 * Dl, ncol = 2 * Dr;
@@ -233,9 +254,25 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-__global__ void __launch_bounds__(SVD_THREADS) svd_kernel(SvdArgs p) {
+__global__ void __launch_bounds__(SVD_THREADS) svd_kernel(const SvdArgs p0, size_t stride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const unsigned long long t_start = global_ns();
+  SvdArgs p = p0;   // this CTA's instance
+  {
+    const size_t io = (size_t)blockIdx.x * stride;
+    p.A = ish(p.A, io);
+    p.scratch = ish(p.scratch, io);
+    p.dims = ish(p.dims, io);
+    p.Vs = ish(p.Vs, io);
+    p.s = ish(p.s, io);
+    p.lam_out = ish(p.lam_out, io);
+    p.W = ish(p.W, io);
+    p.tape_dims = ish(p.tape_dims, io);
+    p.lam_left = ish(p.lam_left, io);
+    p.lam_left_copy = ish(p.lam_left_copy, io);
+    p.status = ish(p.status, io);
+    p.stats = ish(p.stats, io);
+  }
   __shared__ double red[SVD_THREADS / 32];
   __shared__ double s_sh[512];
   __shared__ int flag_sh, conv_sh, k_sh;
@@ -403,7 +440,11 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(SvdArgs p) {
 }
 
 __global__ void vh_rows_kernel(const double2* __restrict__ Vs, const int* __restrict__ dims, int b,
-                               double2* Br) {
+                               double2* Br, size_t stride) {
+  const size_t io = (size_t)blockIdx.y * stride;
+  Vs = ish(Vs, io);
+  dims = ish(dims, io);
+  Br = ish(Br, io);
   const int k = dims[b + 1], ncol = 2 * dims[b + 2];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= k * ncol) return;
@@ -412,7 +453,12 @@ __global__ void vh_rows_kernel(const double2* __restrict__ Vs, const int* __rest
 }
 
 // ---- adjoint pieces -------------------------------------------------------------------------
-__global__ void conjT_kernel(const double2* __restrict__ Bbr, const int* __restrict__ td, double2* Vbar) {
+__global__ void conjT_kernel(const double2* __restrict__ Bbr, const int* __restrict__ td, double2* Vbar,
+                             size_t stride) {
+  const size_t io = (size_t)blockIdx.y * stride;
+  Bbr = ish(Bbr, io);
+  td = ish(td, io);
+  Vbar = ish(Vbar, io);
   const int k = td[3], ncol = 2 * td[2];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= k * ncol) return;
@@ -421,7 +467,12 @@ __global__ void conjT_kernel(const double2* __restrict__ Bbr, const int* __restr
 }
 
 __global__ void sbar_kernel(double* lambar, const double* __restrict__ s, const int* __restrict__ td,
-                            double* wbar) {
+                            double* wbar, size_t stride) {
+  const size_t io = (size_t)blockIdx.x * stride;
+  lambar = ish(lambar, io);
+  s = ish(s, io);
+  td = ish(td, io);
+  wbar = ish(wbar, io);
   const int k = td[3], ncol = td[4];
   __shared__ double nrm_sh, dot_sh;
   if (threadIdx.x == 0) {
@@ -448,7 +499,14 @@ __global__ void sbar_kernel(double* lambar, const double* __restrict__ s, const 
 }
 
 __global__ void build_K_kernel(const double2* __restrict__ Y, const double* __restrict__ s,
-                               const double* __restrict__ wbar, const int* __restrict__ td, double2* Km) {
+                               const double* __restrict__ wbar, const int* __restrict__ td, double2* Km,
+                               size_t stride) {
+  const size_t io = (size_t)blockIdx.y * stride;
+  Y = ish(Y, io);
+  s = ish(s, io);
+  wbar = ish(wbar, io);
+  td = ish(td, io);
+  Km = ish(Km, io);
   const int k = td[3], K = td[4];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= K * K) return;
@@ -468,7 +526,12 @@ __global__ void build_K_kernel(const double2* __restrict__ Y, const double* __re
 }
 
 // Z[r][j] /= w_j (j < k): the complement term (W_k diag(1/w_k)) Z^H of the SVD adjoint
-__global__ void zscale_kernel(double2* Z, const double* __restrict__ s, const int* __restrict__ td) {
+__global__ void zscale_kernel(double2* Z, const double* __restrict__ s, const int* __restrict__ td,
+                              size_t stride) {
+  const size_t io = (size_t)blockIdx.y * stride;
+  Z = ish(Z, io);
+  s = ish(s, io);
+  td = ish(td, io);
   const int k = td[3], n = 2 * td[2];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * k) return;
@@ -478,7 +541,14 @@ __global__ void zscale_kernel(double2* Z, const double* __restrict__ s, const in
 
 __global__ void lam_scale_kernel(double2* Cbar, const double2* __restrict__ Ctbar,
                                  const double2* __restrict__ C, const double* __restrict__ lam_left,
-                                 const int* __restrict__ td, double* lambar_left) {
+                                 const int* __restrict__ td, double* lambar_left, size_t stride) {
+  const size_t io = (size_t)blockIdx.y * stride;
+  Cbar = ish(Cbar, io);
+  Ctbar = ish(Ctbar, io);
+  C = ish(C, io);
+  lam_left = ish(lam_left, io);
+  td = ish(td, io);
+  lambar_left = ish(lambar_left, io);
   const int Dl = td[0], ncol = 2 * td[2];
   const int a = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
@@ -498,7 +568,14 @@ __global__ void lam_scale_kernel(double2* Cbar, const double2* __restrict__ Ctba
 __global__ void __launch_bounds__(256) gbar_kernel(const double2* __restrict__ Cbar,
                                                    const double2* __restrict__ Th, const int* __restrict__ td,
                                                    const double2* __restrict__ dG, double2* Gbar,
-                                                   double* gate_grad) {
+                                                   double* gate_grad, size_t stride) {
+  const size_t io = (size_t)blockIdx.x * stride;
+  Cbar = ish(Cbar, io);
+  Th = ish(Th, io);
+  td = ish(td, io);
+  dG = ish(dG, io);
+  Gbar = ish(Gbar, io);
+  gate_grad = ish(gate_grad, io);
   const int Dl = td[0], Dr = td[2], ncol = 2 * Dr;
   double2 acc[16];
 #pragma unroll
@@ -539,7 +616,12 @@ __global__ void __launch_bounds__(256) gbar_kernel(const double2* __restrict__ C
 }
 
 __global__ void thetabar_kernel(const double2* __restrict__ Cbar, const double2* __restrict__ Gm,
-                                const int* __restrict__ td, double2* Thbar) {
+                                const int* __restrict__ td, double2* Thbar, size_t stride) {
+  const size_t io = (size_t)blockIdx.y * stride;
+  Cbar = ish(Cbar, io);
+  Gm = ish(Gm, io);
+  td = ish(td, io);
+  Thbar = ish(Thbar, io);
   const int Dl = td[0], Dr = td[2], ncol = 2 * Dr;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= Dl * Dr) return;
@@ -558,9 +640,12 @@ __global__ void thetabar_kernel(const double2* __restrict__ Cbar, const double2*
 
 __global__ void theta_reduce_kernel(const double* __restrict__ gate_grad, const int* __restrict__ off,
                                     const int* __restrict__ gidx, const double* __restrict__ scale,
-                                    int n_theta, double* grad) {
+                                    int n_theta, double* grad, size_t stride) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_theta) return;
+  const size_t io = (size_t)blockIdx.y * stride;
+  gate_grad = ish(gate_grad, io);
+  grad = ish(grad, io);
   double acc = 0.0;
   for (int e = off[t]; e < off[t + 1]; ++e) acc += scale[e] * gate_grad[gidx[e]];
   grad[t] = acc;
@@ -570,17 +655,72 @@ inline int cdiv(long long a, int b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
 
-void launch_gate_matrices(const void* d_gates, int n_gates, const double* d_theta, int n_theta, double2* G,
-                          double2* dG, int* status, cudaStream_t st) {
+
+void launch_gate_matrices(const Batch& bt, const void* d_gates, int n_gates, const double* d_theta, int n_theta,
+                          double2* G, double2* dG, int* status, cudaStream_t st) {
   if (n_gates <= 0) return;
-  gate_matrices_kernel<<<cdiv(n_gates, 128), 128, 0, st>>>((const mps_gate*)d_gates, n_gates, d_theta, n_theta,
-                                                           G, dG, status);
+  gate_matrices_kernel<<<dim3(cdiv(n_gates, 128), bt.n), 128, 0, st>>>((const mps_gate*)d_gates, n_gates, d_theta,
+                                                                       n_theta, G, dG, status, bt.stride);
   note_launch();
 }
 
-void launch_contract(const double2* Bl, const double2* Br, const int* dims, int b, const double2* G,
-                     const double* lam_left, double2* C, double2* A, int max_dl, int max_dr, cudaStream_t st) {
-  contract_kernel<<<cdiv((long long)max_dl * max_dr, 128), 128, 0, st>>>(Bl, Br, dims, b, G, lam_left, C, A);
+void launch_contract(const Batch& bt, const double2* Bl, const double2* Br, const int* dims, int b,
+                     const double2* G, const double* lam_left, double2* C, double2* A, double2* Bl_tape,
+                     double2* Br_tape, int max_dl, int max_dr, cudaStream_t st) {
+  contract_kernel<<<dim3(cdiv((long long)max_dl * max_dr, 128), bt.n), 128, 0, st>>>(
+      Bl, Br, dims, b, G, lam_left, C, A, Bl_tape, Br_tape, bt.stride);
+  note_launch();
+}
+
+namespace {
+__global__ void copy_f64_kernel(double* __restrict__ dst, size_t dst_stride, const double* __restrict__ src,
+                                size_t src_stride, size_t n) {
+  dst = ish(dst, (size_t)blockIdx.y * dst_stride);
+  src = ish(src, (size_t)blockIdx.y * src_stride);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+__global__ void zero_f64_kernel(double* __restrict__ dst, size_t stride, size_t n) {
+  dst = ish(dst, (size_t)blockIdx.y * stride);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = 0.0;
+}
+
+// out[0] = first non-zero status over the instances (0 if none), out[1] = that instance;
+// every status word is cleared.
+__global__ void status_fetch_kernel(int* status, size_t stride, int n_inst, double* out) {
+  double code = 0.0, which = -1.0;
+  for (int i = 0; i < n_inst; ++i) {
+    int* si = ish(status, (size_t)i * stride);
+    if (*si != 0 && code == 0.0) {
+      code = (double)*si;
+      which = (double)i;
+    }
+    *si = 0;
+  }
+  out[0] = code;
+  out[1] = which;
+}
+}  // namespace
+
+void launch_copy_f64(const Batch& bt, double* dst, size_t dst_stride, const double* src, size_t src_stride,
+                     size_t n, cudaStream_t st) {
+  if (n == 0) return;
+  const long long blocks = std::min<long long>(cdiv((long long)n, 256), 152LL * 4);
+  copy_f64_kernel<<<dim3((unsigned)blocks, bt.n), 256, 0, st>>>(dst, dst_stride, src, src_stride, n);
+  note_launch();
+}
+
+void launch_zero_f64(const Batch& bt, double* dst, size_t n, cudaStream_t st) {
+  if (n == 0) return;
+  const long long blocks = std::min<long long>(cdiv((long long)n, 256), 152LL * 4);
+  zero_f64_kernel<<<dim3((unsigned)blocks, bt.n), 256, 0, st>>>(dst, bt.stride, n);
+  note_launch();
+}
+
+void launch_status_fetch(const Batch& bt, int* status, double* out, cudaStream_t st) {
+  status_fetch_kernel<<<1, 1, 0, st>>>(status, bt.stride, bt.n, out);
   note_launch();
 }
 
@@ -615,68 +755,73 @@ static size_t svd_dynamic_limit() {
 
 bool svd_fits_smem(int m_cap, int n_cap) { return svd_smem_bytes(m_cap, n_cap) <= svd_dynamic_limit(); }
 
-void launch_svd(const SvdArgs& a, int m_cap, int n_cap, cudaStream_t st) {
+void launch_svd(const Batch& bt, const SvdArgs& a, int m_cap, int n_cap, cudaStream_t st) {
   SvdArgs b = a;
   size_t smem = 0;
   if (svd_fits_smem(m_cap, n_cap)) {
     b.scratch = nullptr;
     smem = svd_smem_bytes(m_cap, n_cap);
   }
-  svd_kernel<<<1, SVD_THREADS, smem, st>>>(b);
+  svd_kernel<<<bt.n, SVD_THREADS, smem, st>>>(b, bt.stride);
   note_launch();
 }
 
-void launch_vh_rows(const double2* Vs, const int* dims, int b, double2* Br_out, int max_k, int max_ncol,
-                    cudaStream_t st) {
-  vh_rows_kernel<<<cdiv((long long)max_k * max_ncol, 256), 256, 0, st>>>(Vs, dims, b, Br_out);
+void launch_vh_rows(const Batch& bt, const double2* Vs, const int* dims, int b, double2* Br_out, int max_k,
+                    int max_ncol, cudaStream_t st) {
+  vh_rows_kernel<<<dim3(cdiv((long long)max_k * max_ncol, 256), bt.n), 256, 0, st>>>(Vs, dims, b, Br_out,
+                                                                                     bt.stride);
   note_launch();
 }
 
-void launch_conjT(const double2* Bbar_r, const int* td, double2* Vbar, int max_k, int max_ncol, cudaStream_t st) {
-  conjT_kernel<<<cdiv((long long)max_k * max_ncol, 256), 256, 0, st>>>(Bbar_r, td, Vbar);
+void launch_conjT(const Batch& bt, const double2* Bbar_r, const int* td, double2* Vbar, int max_k, int max_ncol,
+                  cudaStream_t st) {
+  conjT_kernel<<<dim3(cdiv((long long)max_k * max_ncol, 256), bt.n), 256, 0, st>>>(Bbar_r, td, Vbar, bt.stride);
   note_launch();
 }
 
-void launch_sbar(double* lambar_slot, const double* s, const int* td, double* wbar, int max_ncol,
+void launch_sbar(const Batch& bt, double* lambar_slot, const double* s, const int* td, double* wbar,
                  cudaStream_t st) {
-  (void)max_ncol;
-  sbar_kernel<<<1, 256, 0, st>>>(lambar_slot, s, td, wbar);
+  sbar_kernel<<<bt.n, 256, 0, st>>>(lambar_slot, s, td, wbar, bt.stride);
   note_launch();
 }
 
-void launch_build_K(const double2* Y, const double* s, const double* wbar, const int* td, double2* K,
-                    int max_K, cudaStream_t st) {
-  build_K_kernel<<<cdiv((long long)max_K * max_K, 256), 256, 0, st>>>(Y, s, wbar, td, K);
+void launch_build_K(const Batch& bt, const double2* Y, const double* s, const double* wbar, const int* td,
+                    double2* K, int max_K, cudaStream_t st) {
+  build_K_kernel<<<dim3(cdiv((long long)max_K * max_K, 256), bt.n), 256, 0, st>>>(Y, s, wbar, td, K, bt.stride);
   note_launch();
 }
 
-void launch_zscale(double2* Z, const double* s, const int* td, int max_n, int max_k, cudaStream_t st) {
-  zscale_kernel<<<cdiv((long long)max_n * max_k, 256), 256, 0, st>>>(Z, s, td);
+void launch_zscale(const Batch& bt, double2* Z, const double* s, const int* td, int max_n, int max_k,
+                   cudaStream_t st) {
+  zscale_kernel<<<dim3(cdiv((long long)max_n * max_k, 256), bt.n), 256, 0, st>>>(Z, s, td, bt.stride);
   note_launch();
 }
 
-void launch_lam_scale(double2* Cbar, const double2* Ctbar, const double2* C, const double* lam_left,
-                      const int* td, double* lambar_left, int max_dl, cudaStream_t st) {
-  lam_scale_kernel<<<cdiv(max_dl, 8), 256, 0, st>>>(Cbar, Ctbar, C, lam_left, td, lambar_left);
+void launch_lam_scale(const Batch& bt, double2* Cbar, const double2* Ctbar, const double2* C,
+                      const double* lam_left, const int* td, double* lambar_left, int max_dl, cudaStream_t st) {
+  lam_scale_kernel<<<dim3(cdiv(max_dl, 8), bt.n), 256, 0, st>>>(Cbar, Ctbar, C, lam_left, td, lambar_left,
+                                                                bt.stride);
   note_launch();
 }
 
-void launch_gbar(const double2* Cbar, const double2* Theta, const int* td, const double2* dG, double2* Gbar,
-                 double* gate_grad, cudaStream_t st) {
-  gbar_kernel<<<1, 256, 0, st>>>(Cbar, Theta, td, dG, Gbar, gate_grad);
+void launch_gbar(const Batch& bt, const double2* Cbar, const double2* Theta, const int* td, const double2* dG,
+                 double2* Gbar, double* gate_grad, cudaStream_t st) {
+  gbar_kernel<<<bt.n, 256, 0, st>>>(Cbar, Theta, td, dG, Gbar, gate_grad, bt.stride);
   note_launch();
 }
 
-void launch_thetabar(const double2* Cbar, const double2* G, const int* td, double2* Thbar, int max_dl, int max_dr,
-                     cudaStream_t st) {
-  thetabar_kernel<<<cdiv((long long)max_dl * max_dr, 128), 128, 0, st>>>(Cbar, G, td, Thbar);
+void launch_thetabar(const Batch& bt, const double2* Cbar, const double2* G, const int* td, double2* Thbar,
+                     int max_dl, int max_dr, cudaStream_t st) {
+  thetabar_kernel<<<dim3(cdiv((long long)max_dl * max_dr, 128), bt.n), 128, 0, st>>>(Cbar, G, td, Thbar,
+                                                                                     bt.stride);
   note_launch();
 }
 
-void launch_theta_reduce(const double* gate_grad, const int* csr_off, const int* csr_gate, const double* csr_scale,
-                         int n_theta, double* grad, cudaStream_t st) {
+void launch_theta_reduce(const Batch& bt, const double* gate_grad, const int* csr_off, const int* csr_gate,
+                         const double* csr_scale, int n_theta, double* grad, cudaStream_t st) {
   if (n_theta <= 0) return;
-  theta_reduce_kernel<<<cdiv(n_theta, 128), 128, 0, st>>>(gate_grad, csr_off, csr_gate, csr_scale, n_theta, grad);
+  theta_reduce_kernel<<<dim3(cdiv(n_theta, 128), bt.n), 128, 0, st>>>(gate_grad, csr_off, csr_gate, csr_scale,
+                                                                      n_theta, grad, bt.stride);
   note_launch();
 }
 

@@ -28,9 +28,13 @@ __device__ __forceinline__ double2 load_op(const double2* X, int ld, int op, int
   }
 }
 
-__device__ __forceinline__ void gemm_tile(const GemmDesc& d) {
+__device__ __forceinline__ void gemm_tile(const GemmDesc& d0, int row0, int col0, size_t io) {
+  GemmDesc d = d0;
+  d.A = ish(d.A, io);
+  d.B = ish(d.B, io);
+  d.C = ish(d.C, io);
+  d.dims = ish(d.dims, io);
   const int M = deval(d.M, d.dims), N = deval(d.N, d.dims), K = deval(d.K, d.dims);
-  const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TN;
   if (row0 >= M || col0 >= N || M <= 0 || N <= 0) return;
   const int lda = deval(d.lda, d.dims), ldb = deval(d.ldb, d.dims), ldc = deval(d.ldc, d.dims);
   __shared__ double2 As[TK][TM + 1];
@@ -84,16 +88,26 @@ __device__ __forceinline__ void gemm_tile(const GemmDesc& d) {
   }
 }
 
-__global__ void __launch_bounds__(256) zgemm_batched_kernel(const GemmDesc* __restrict__ descs) {
-  gemm_tile(descs[blockIdx.z]);
+// grid: x = column tile, y = row tile + tiles_m * instance, z = descriptor
+__global__ void __launch_bounds__(256) zgemm_batched_kernel(const GemmDesc* __restrict__ descs, int tiles_m,
+                                                            size_t stride) {
+  const int inst = blockIdx.y / tiles_m, tm = blockIdx.y - inst * tiles_m;
+  gemm_tile(descs[blockIdx.z], tm * TM, blockIdx.x * TN, (size_t)inst * stride);
 }
 
 // Small per-gate GEMMs: 16 x 16 outputs per CTA, one per thread.  FP64 is the bound, so the
 // work is spread over as many SMs as the output allows (a 64 x 64 output uses 16 CTAs).
 constexpr int SM_T = 16, SK = 16;
 
-__global__ void __launch_bounds__(256) zgemm_small_kernel(const GemmBatch batch) {
-  const GemmDesc& d = batch.d[blockIdx.z];
+// grid: x = column tile, y = row tile, z = descriptor + count * instance
+__global__ void __launch_bounds__(256) zgemm_small_kernel(const GemmBatch batch, size_t stride) {
+  const int inst = blockIdx.z / batch.count;
+  const size_t io = (size_t)inst * stride;
+  GemmDesc d = batch.d[blockIdx.z - inst * batch.count];
+  d.A = ish(d.A, io);
+  d.B = ish(d.B, io);
+  d.C = ish(d.C, io);
+  d.dims = ish(d.dims, io);
   const int M = deval(d.M, d.dims), N = deval(d.N, d.dims), K = deval(d.K, d.dims);
   const int row0 = blockIdx.y * SM_T, col0 = blockIdx.x * SM_T;
   if (row0 >= M || col0 >= N || M <= 0 || N <= 0) return;
@@ -126,17 +140,19 @@ __global__ void __launch_bounds__(256) zgemm_small_kernel(const GemmBatch batch)
 
 }  // namespace
 
-void launch_zgemm_small(const GemmBatch& b, int max_m, int max_n, cudaStream_t st) {
+void launch_zgemm_small(const Batch& bt, const GemmBatch& b, int max_m, int max_n, cudaStream_t st) {
   if (b.count <= 0 || max_m <= 0 || max_n <= 0) return;
-  dim3 grid((max_n + SM_T - 1) / SM_T, (max_m + SM_T - 1) / SM_T, b.count);
-  zgemm_small_kernel<<<grid, 256, 0, st>>>(b);
+  dim3 grid((max_n + SM_T - 1) / SM_T, (max_m + SM_T - 1) / SM_T, b.count * bt.n);
+  zgemm_small_kernel<<<grid, 256, 0, st>>>(b, bt.stride);
   note_launch();
 }
 
-void launch_zgemm_batched(const GemmDesc* d_descs, int count, int max_m, int max_n, cudaStream_t st) {
+void launch_zgemm_batched(const Batch& bt, const GemmDesc* d_descs, int count, int max_m, int max_n,
+                          cudaStream_t st) {
   if (count <= 0 || max_m <= 0 || max_n <= 0) return;
-  dim3 grid((max_n + TN - 1) / TN, (max_m + TM - 1) / TM, count);
-  zgemm_batched_kernel<<<grid, 256, 0, st>>>(d_descs);
+  const int tiles_m = (max_m + TM - 1) / TM;
+  dim3 grid((max_n + TN - 1) / TN, tiles_m * bt.n, count);
+  zgemm_batched_kernel<<<grid, 256, 0, st>>>(d_descs, tiles_m, bt.stride);
   note_launch();
 }
 

@@ -48,9 +48,23 @@ mps_status fail(mps_status st, const std::string& msg) {
 }
 void clear_error() { g_err.clear(); }
 
+// Waits for the legacy default stream, on which allocations are zeroed and host tables are
+// uploaded (cudaMemset/cudaMemcpy).  A pageable host-to-device cudaMemcpy may return before its
+// DMA has landed, and the library's kernels run on non-blocking streams that do not order
+// themselves after the legacy stream, so every such batch ends with this fence.
+mps_status legacy_fence() {
+  MPS_CU(cudaStreamSynchronize(cudaStreamLegacy));
+  return MPS_OK;
+}
+
 mps_status DevBuf::alloc(size_t nbytes) {
   reset();
   if (nbytes == 0) nbytes = 16;
+  if (arena) {
+    MPS_TRY(arena->alloc(nbytes, &p));
+    bytes = nbytes;
+    return MPS_OK;
+  }
   cudaError_t e = cudaMalloc(&p, nbytes);
   if (e != cudaSuccess) {
     p = nullptr;
@@ -59,7 +73,7 @@ mps_status DevBuf::alloc(size_t nbytes) {
   }
   bytes = nbytes;
   MPS_CU(cudaMemset(p, 0, nbytes));
-  return MPS_OK;
+  return legacy_fence();
 }
 
 mps_status DevBuf::ensure(size_t nbytes) {
@@ -100,7 +114,8 @@ mps_status StateBuf::alloc(const Layout& L) {
 
 mps_status StateBuf::copy_from(const StateBuf& o, const Layout& L, cudaStream_t st) {
   (void)L;
-  MPS_CU(cudaMemcpyAsync(mem.p, o.mem.p, mem.bytes, cudaMemcpyDeviceToDevice, st));
+  const Batch bt = mem.arena ? mem.arena->batch() : Batch{1, 0};
+  launch_copy_f64(bt, mem.as<double>(), bt.stride, o.mem.as<double>(), bt.stride, mem.bytes / sizeof(double), st);
   return MPS_OK;
 }
 
@@ -122,7 +137,9 @@ struct TapeSlot {
   int* dims;
 };
 
+// Every device buffer of a workspace is per instance (a range of the state's arena).
 struct Workspace {
+  Arena* arena;
   DevBuf A, svd, C, Vs, s;                        // forward scratch at the largest bond
   DevBuf G, dG, theta, scalars, gate_grad, grad;  // per call
   StateBuf work, rec;                             // energy_grad working states
@@ -138,16 +155,36 @@ struct Workspace {
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  DevBuf stats;            // 4 doubles on the device: FP64 flops, FP32 flops, SVD ns, SVD launches
+  DevBuf stats;            // 4 doubles per instance: FP64 flops, FP32 flops, SVD ns, SVD launches
   double svd_ms = 0.0;
   long long svd_launches = 0;
   // captured energy+gradient call (see mps_energy_grad_dev)
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<const void*> graph_key, graph_seen;
   long long graph_kernels = 0;
+  // Host inputs and outputs of a call pass through pinned host memory that kernels read and
+  // write directly (slot 0 receives the status word).  No call queues work on a copy engine:
+  // copy-engine queues are shared by all streams, so an output copy that waits for one
+  // evaluation would hold back every other evaluation behind it.
+  double* stage = nullptr;        // host view
+  double* stage_dev = nullptr;    // device view
+  size_t stage_n = 0, stage_used = 0;
+  struct Pending {
+    double* dst;
+    size_t off, count;
+  };
+  std::vector<Pending> pending;   // host outputs to copy out of the staging after the call
+  cudaEvent_t done = nullptr;     // blocking-sync event: waiting threads sleep instead of spinning
+  long long auto_uid = -1;        // circuit for which the automatic checkpoint interval was chosen
+  int auto_K = 0;
+  explicit Workspace(Arena* a)
+      : arena(a), A(a), svd(a), C(a), Vs(a), s(a), G(a), dG(a), theta(a), scalars(a), gate_grad(a), grad(a),
+        work(a), rec(a), tape(a), Bbar(a), lambar(a), rv(a), stats(a) {}
   ~Workspace() {
     for (auto e : ev_pool) cudaEventDestroy(e);
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (stage) cudaFreeHost(stage);
+    if (done) cudaEventDestroy(done);
   }
 };
 
@@ -157,6 +194,7 @@ struct Ctx {
   cudaStream_t st;
   int* status;
   Workspace* ws;
+  Batch bt;
 };
 
 static mps_status ensure_forward_scratch(const Layout& L, Workspace& w) {
@@ -196,15 +234,11 @@ static mps_status forward_gate(Ctx& cx, StateBuf& sb, int b, const double2* Gt, 
   Workspace& w = *cx.ws;
   double2* Bl = sb.B + L.site_off[b];
   double2* Br = sb.B + L.site_off[b + 1];
-  if (tp) {
-    MPS_CU(cudaMemcpyAsync(tp->Bl, Bl, L.site_cap(b) * sizeof(double2), cudaMemcpyDeviceToDevice, cx.st));
-    MPS_CU(cudaMemcpyAsync(tp->Br, Br, L.site_cap(b + 1) * sizeof(double2), cudaMemcpyDeviceToDevice, cx.st));
-  }
   double2* C = tp ? tp->C : w.C.as<double2>();
   double2* Vs = tp ? tp->Vs : w.Vs.as<double2>();
   double* s = tp ? tp->s : w.s.as<double>();
-  launch_contract(Bl, Br, sb.dims, b, Gt, sb.lam + L.lam_off[b], C, w.A.as<double2>(), L.cap[b], L.cap[b + 2],
-                  cx.st);
+  launch_contract(cx.bt, Bl, Br, sb.dims, b, Gt, sb.lam + L.lam_off[b], C, w.A.as<double2>(), tp ? tp->Bl : nullptr,
+                  tp ? tp->Br : nullptr, L.cap[b], L.cap[b + 2], cx.st);
   SvdArgs a{};
   a.A = w.A.as<double2>();
   a.scratch = w.svd.as<double2>();
@@ -231,7 +265,7 @@ static mps_status forward_gate(Ctx& cx, StateBuf& sb, int b, const double2* Gt, 
     }
     MPS_CU(cudaEventRecord(w.ev_pool[w.ev_used], cx.st));
   }
-  launch_svd(a, 2 * L.cap[b], 2 * L.cap[b + 2], cx.st);
+  launch_svd(cx.bt, a, 2 * L.cap[b], 2 * L.cap[b + 2], cx.st);
   if (w.profile) {
     MPS_CU(cudaEventRecord(w.ev_pool[w.ev_used + 1], cx.st));
     w.ev_used += 2;
@@ -240,8 +274,8 @@ static mps_status forward_gate(Ctx& cx, StateBuf& sb, int b, const double2* Gt, 
   g.count = 1;
   g.d[0] = make_desc(sb.dims, C, OP_N, Vs, OP_T, Bl, dref(b, 2), dref(b + 1), dref(b + 2, 2), dref(b + 2, 2),
                      dref(b + 2, 2), dref(b + 1));
-  launch_zgemm_small(g, 2 * L.cap[b], L.cap[b + 1], cx.st);
-  launch_vh_rows(Vs, sb.dims, b, Br, L.cap[b + 1], 2 * L.cap[b + 2], cx.st);
+  launch_zgemm_small(cx.bt, g, 2 * L.cap[b], L.cap[b + 1], cx.st);
+  launch_vh_rows(cx.bt, Vs, sb.dims, b, Br, L.cap[b + 1], 2 * L.cap[b + 2], cx.st);
   return MPS_OK;
 }
 
@@ -266,35 +300,35 @@ static mps_status reverse_gate(Ctx& cx, int t, int b, const TapeSlot& tp, double
   double2* Bbl = Bbar + L.site_off[b];
   double2* Bbr = Bbar + L.site_off[b + 1];
   const int mcap = 2 * L.cap[b], ncap = 2 * L.cap[b + 2], kcap = L.cap[b + 1], Kcap = std::min(mcap, ncap);
-  launch_conjT(Bbr, td, w.Vbar, kcap, ncap, cx.st);                          // Vbar = Bbar_{b+1}^H
+  launch_conjT(cx.bt, Bbr, td, w.Vbar, kcap, ncap, cx.st);                          // Vbar = Bbar_{b+1}^H
   GemmBatch g{};
   g.count = 3;
   g.d[0] = make_desc(td, tp.C, OP_H, Bbl, OP_N, w.Vbar, nc, k, m, nc, k, k, true);     // Vbar += C^H Bbar_b
   g.d[1] = make_desc(td, Bbl, OP_N, tp.Vs, OP_C, w.Cbar, m, nc, k, k, nc, nc);         // Cbar = Bbar_b V_k^H
   g.d[2] = make_desc(td, tp.Bl, OP_N, tp.Br, OP_N, w.Theta, m, nc, Dm, Dm, nc, nc);    // Theta = B_b B_{b+1}
-  launch_zgemm_small(g, std::max(mcap, ncap), std::max(kcap, ncap), cx.st);
-  launch_sbar(lambar + L.lam_off[b + 1], tp.s, td, w.wbar, Kcap, cx.st);              // sbar -> wbar
+  launch_zgemm_small(cx.bt, g, std::max(mcap, ncap), std::max(kcap, ncap), cx.st);
+  launch_sbar(cx.bt, lambar + L.lam_off[b + 1], tp.s, td, w.wbar, cx.st);              // sbar -> wbar
   g.count = 1;
   g.d[0] = make_desc(td, tp.Vs, OP_C, w.Vbar, OP_N, w.Y, Ks, k, nc, nc, k, k);         // Y = V_e^H Vbar
-  launch_zgemm_small(g, Kcap, kcap, cx.st);
+  launch_zgemm_small(cx.bt, g, Kcap, kcap, cx.st);
   g.d[0] = make_desc(td, tp.Vs, OP_T, w.Y, OP_N, w.Vbar, nc, k, Ks, nc, k, k, true, -1.0);   // Z = Vbar - V_e Y
-  launch_zgemm_small(g, ncap, kcap, cx.st);
-  launch_build_K(w.Y, tp.s, w.wbar, td, w.Km, Kcap, cx.st);                            // diag(wbar)+J+J^H
-  launch_zscale(w.Vbar, tp.s, td, ncap, kcap, cx.st);                                  // Z diag(1/w_k)
+  launch_zgemm_small(cx.bt, g, ncap, kcap, cx.st);
+  launch_build_K(cx.bt, w.Y, tp.s, w.wbar, td, w.Km, Kcap, cx.st);                            // diag(wbar)+J+J^H
+  launch_zscale(cx.bt, w.Vbar, tp.s, td, ncap, kcap, cx.st);                                  // Z diag(1/w_k)
   g.d[0] = make_desc(td, tp.W, OP_T, w.Km, OP_N, w.T1, m, Ks, Ks, m, Ks, Ks);          // T1 = W K
-  launch_zgemm_small(g, mcap, Kcap, cx.st);
+  launch_zgemm_small(cx.bt, g, mcap, Kcap, cx.st);
   g.d[0] = make_desc(td, w.T1, OP_N, tp.Vs, OP_C, w.Ctbar, m, nc, Ks, Ks, nc, nc);     // C~bar = T1 V_e^H
-  launch_zgemm_small(g, mcap, ncap, cx.st);
+  launch_zgemm_small(cx.bt, g, mcap, ncap, cx.st);
   g.d[0] = make_desc(td, tp.W, OP_T, w.Vbar, OP_H, w.Ctbar, m, nc, k, m, k, nc, true);  // += W_k (Z/w)^H
-  launch_zgemm_small(g, mcap, ncap, cx.st);
-  launch_lam_scale(w.Cbar, w.Ctbar, tp.C, tp.lamL, td, b > 0 ? lambar + L.lam_off[b] : nullptr, L.cap[b],
+  launch_zgemm_small(cx.bt, g, mcap, ncap, cx.st);
+  launch_lam_scale(cx.bt, w.Cbar, w.Ctbar, tp.C, tp.lamL, td, b > 0 ? lambar + L.lam_off[b] : nullptr, L.cap[b],
                    cx.st);
-  launch_gbar(w.Cbar, w.Theta, td, dG + 16 * (size_t)t, w.Gbar, gate_grad + t, cx.st);
-  launch_thetabar(w.Cbar, G + 16 * (size_t)t, td, w.Thbar, L.cap[b], L.cap[b + 2], cx.st);
+  launch_gbar(cx.bt, w.Cbar, w.Theta, td, dG + 16 * (size_t)t, w.Gbar, gate_grad + t, cx.st);
+  launch_thetabar(cx.bt, w.Cbar, G + 16 * (size_t)t, td, w.Thbar, L.cap[b], L.cap[b + 2], cx.st);
   g.count = 2;
   g.d[0] = make_desc(td, w.Thbar, OP_N, tp.Br, OP_H, Bbl, m, Dm, nc, nc, nc, Dm);      // Bbar_b = Thbar B_{b+1}^H
   g.d[1] = make_desc(td, tp.Bl, OP_H, w.Thbar, OP_N, Bbr, Dm, nc, m, Dm, nc, nc);      // Bbar_{b+1} = B_b^H Thbar
-  launch_zgemm_small(g, std::max(mcap, kcap), std::max(kcap, ncap), cx.st);
+  launch_zgemm_small(cx.bt, g, std::max(mcap, kcap), std::max(kcap, ncap), cx.st);
   return MPS_OK;
 }
 
@@ -311,7 +345,11 @@ struct Step {
   int slot = 0;
 };
 
+// Energy plan of one Hamiltonian for one state: `bufs` is per instance (a range of the state's
+// arena); the descriptor and pointer tables are shared by the instances and hold instance-0
+// addresses, which the kernels shift.
 struct EnergyCache {
+  long long key_arena = 0;
   const void* key_B = nullptr;
   const int* key_dims = nullptr;
   const void* key_Bbar = nullptr;
@@ -393,11 +431,14 @@ static mps_status build_energy_cache(const Layout& L, const StateBuf& sb, mps_ha
     if (is_parent[v] && s + 1 < n) oT[v] = take(site_sz(s + 1));
   }
   size_t o_e = take(2 * (size_t)std::max(nt, 1));
+  Arena* arena = sb.mem.arena;
+  ec.bufs.arena = arena;
   MPS_TRY(ec.bufs.alloc(total * sizeof(double2)));
   double2* base = ec.bufs.as<double2>();
   auto P = [&](size_t o) { return base + o; };
   double2 one_val = make_double2(1.0, 0.0);
-  MPS_CU(cudaMemcpy(P(o_one), &one_val, sizeof(double2), cudaMemcpyHostToDevice));
+  for (int i = 0; i < arena->n; ++i)
+    MPS_CU(cudaMemcpy(ish(P(o_one), (size_t)i * arena->stride), &one_val, sizeof(double2), cudaMemcpyHostToDevice));
   ec.e = P(o_e);
   ec.Z = P(oLI[n - 1]);
   ec.OB = base;
@@ -682,17 +723,19 @@ static mps_status build_energy_cache(const Layout& L, const StateBuf& sb, mps_ha
   ec.d_nodeop = reinterpret_cast<int*>(tbase + t_op);
   ec.d_site_off = reinterpret_cast<size_t*>(tbase + t_so);
   ec.d_ob_off = reinterpret_cast<size_t*>(tbase + t_ob);
+  ec.key_arena = arena->uid;
   ec.key_B = sb.B;
   ec.key_dims = sb.dims;
   ec.key_Bbar = d_Bbar;
-  return MPS_OK;
+  return legacy_fence();
 }
 
 // Energy (and, when d_Bbar != null, the cotangent dE/dB* written in the state's site layout).
 static mps_status energy_pass_impl(const Layout& L, const StateBuf& sb, cudaStream_t st, int* status,
                                    mps_hamiltonian_dev* h, double* d_E, double* d_expect, double2* d_Bbar) {
-  if (!h->cache || h->cache->key_B != sb.B || h->cache->key_dims != sb.dims ||
-      (d_Bbar && h->cache->key_Bbar != d_Bbar)) {
+  const Batch bt = sb.mem.arena->batch();
+  if (!h->cache || h->cache->key_arena != sb.mem.arena->uid || h->cache->key_B != sb.B ||
+      h->cache->key_dims != sb.dims || (d_Bbar && h->cache->key_Bbar != d_Bbar)) {
     MPS_CU(cudaStreamSynchronize(st));
     h->cache.reset(new EnergyCache());
     MPS_TRY(build_energy_cache(L, sb, h, d_Bbar, *h->cache));
@@ -702,22 +745,22 @@ static mps_status energy_pass_impl(const Layout& L, const StateBuf& sb, cudaStre
   auto run = [&](const std::vector<Step>& plan) -> mps_status {
     for (const Step& s : plan) {
       switch (s.kind) {
-        case Step::GEMM: launch_zgemm_batched(ec.d_desc + s.off, s.count, s.max_m, s.max_n, st); break;
+        case Step::GEMM: launch_zgemm_batched(bt, ec.d_desc + s.off, s.count, s.max_m, s.max_n, st); break;
         case Step::AXPY:
-          launch_axpy_lists(ec.d_axpy + s.off, s.count, ec.d_src, ec.d_srccoef, sb.dims, s.max_m, st);
+          launch_axpy_lists(bt, ec.d_axpy + s.off, s.count, ec.d_src, ec.d_srccoef, sb.dims, s.max_m, st);
           break;
         case Step::PAULIS:
-          launch_apply_paulis(sb.B, ec.d_site_off, ec.d_ob_off, sb.dims, L.n, ec.OB, ec.max_site, st);
+          launch_apply_paulis(bt, sb.B, ec.d_site_off, ec.d_ob_off, sb.dims, L.n, ec.OB, ec.max_site, st);
           break;
-        case Step::DOTS: launch_env_dots(ec.d_dotL, ec.d_dotR, ec.d_dotdidx, sb.dims, nt, ec.e, st); break;
+        case Step::DOTS: launch_env_dots(bt, ec.d_dotL, ec.d_dotR, ec.d_dotdidx, sb.dims, nt, ec.e, st); break;
         case Step::SUM:
-          launch_energy_sum(ec.e, h->d_coeff.as<double>(), nt, h->c0, ec.Z, d_E, d_expect, status, st);
+          launch_energy_sum(bt, ec.e, h->d_coeff.as<double>(), nt, h->c0, ec.Z, d_E, d_expect, status, st);
           break;
         case Step::RSUM:
-          launch_rsum(ec.Rsum[s.slot], ec.AR[s.slot], ec.RI[s.slot], h->c0, d_E, sb.dims, s.slot, s.max_m, st);
+          launch_rsum(bt, ec.Rsum[s.slot], ec.AR[s.slot], ec.RI[s.slot], h->c0, d_E, sb.dims, s.slot, s.max_m, st);
           break;
         case Step::SEED:
-          launch_seed_assemble(ec.d_seed, L.n, ec.d_Enode, ec.d_nodeop, sb.dims, ec.Z, ec.max_site, st);
+          launch_seed_assemble(bt, ec.d_seed, L.n, ec.d_Enode, ec.d_nodeop, sb.dims, ec.Z, ec.max_site, st);
           break;
       }
     }
@@ -823,21 +866,6 @@ static mps_status harvest_profile(Workspace& w) {
   return MPS_OK;
 }
 
-mps_status check_status_word(cudaStream_t st, DevBuf& status, const char* where) {
-  MPS_CU(cudaStreamSynchronize(st));
-  int code = 0;
-  MPS_CU(cudaMemcpy(&code, status.p, sizeof(int), cudaMemcpyDeviceToHost));
-  if (code != 0) {
-    MPS_CU(cudaMemset(status.p, 0, sizeof(int)));
-    const char* what = code == MPS_ENOCONV   ? "Jacobi SVD did not converge"
-                       : code == MPS_ENUMERIC ? "non-finite or zero norm met on the device"
-                       : code == MPS_EINVAL   ? "invalid angle index or non-finite angle"
-                                              : "device error";
-    return fail((mps_status)code, std::string(where) + ": " + what);
-  }
-  return MPS_OK;
-}
-
 static mps_status validate_config(const mps_config* cfg) {
   if (!cfg) return fail(MPS_EINVAL, "config is NULL");
   if (cfg->max_bond < 1 || cfg->max_bond > 256)
@@ -848,32 +876,90 @@ static mps_status validate_config(const mps_config* cfg) {
   return MPS_OK;
 }
 
-// theta (host or device) -> device copy in the workspace
-static mps_status stage_theta(mps_state* s, const double* theta, int n_theta, const double** d_theta) {
+// Starts a call: staging room for `count` doubles of host inputs and outputs per instance
+// (plus the status).
+static mps_status begin_call(mps_state* s, size_t count) {
   Workspace& w = *s->ws;
-  if (n_theta < 0) return fail(MPS_EINVAL, "n_theta < 0");
-  if (n_theta > 0 && !theta) return fail(MPS_EINVAL, "theta is NULL");
-  MPS_TRY(w.theta.ensure(std::max(1, n_theta) * sizeof(double)));
-  if (n_theta == 0) {
-    *d_theta = w.theta.as<double>();
-    return MPS_OK;
+  count = count * (size_t)s->n_inst() + 2;
+  if (!w.stage || w.stage_n < count) {
+    if (w.stage) cudaFreeHost(w.stage);
+    w.stage = w.stage_dev = nullptr;
+    w.stage_n = 0;
+    MPS_CU(cudaHostAlloc(reinterpret_cast<void**>(&w.stage), count * sizeof(double), cudaHostAllocMapped));
+    MPS_CU(cudaHostGetDevicePointer(reinterpret_cast<void**>(&w.stage_dev), w.stage, 0));
+    w.stage_n = count;
   }
-  if (is_device_ptr(theta)) {   // finiteness is checked by the gate-matrix kernel
-    MPS_CU(cudaMemcpyAsync(w.theta.p, theta, n_theta * sizeof(double), cudaMemcpyDeviceToDevice, s->st));
-    *d_theta = w.theta.as<double>();
-    return MPS_OK;
-  }
-  for (int i = 0; i < n_theta; ++i)
-    if (!std::isfinite(theta[i])) return fail(MPS_EINVAL, "theta contains a non-finite value");
-  MPS_CU(cudaMemcpyAsync(w.theta.p, theta, n_theta * sizeof(double), cudaMemcpyHostToDevice, s->st));
-  *d_theta = w.theta.as<double>();
+  w.stage_used = 2;
+  w.pending.clear();
   return MPS_OK;
 }
 
-static mps_status put_out(double* dst, const double* dsrc, size_t count, cudaStream_t st) {
+static size_t stage_take(Workspace& w, size_t count) {
+  const size_t o = w.stage_used;
+  w.stage_used += count;
+  return o;
+}
+
+// Ends a call: fetch the status word through the staging, wait for the stream, and copy the
+// host outputs out only when the call succeeded (outputs are untouched on error).
+static mps_status finish_call(mps_state* s, const char* where) {
+  Workspace& w = *s->ws;
+  launch_status_fetch(s->batch(), s->status.as<int>(), w.stage_dev, s->st);
+  if (!w.done) MPS_CU(cudaEventCreateWithFlags(&w.done, cudaEventBlockingSync | cudaEventDisableTiming));
+  MPS_CU(cudaEventRecord(w.done, s->st));
+  MPS_CU(cudaEventSynchronize(w.done));
+  const int code = (int)w.stage[0];
+  if (code != 0) {
+    const char* what = code == MPS_ENOCONV   ? "Jacobi SVD did not converge"
+                       : code == MPS_ENUMERIC ? "non-finite or zero norm met on the device"
+                       : code == MPS_EINVAL   ? "invalid angle index or non-finite angle"
+                                              : "device error";
+    std::string inst = s->n_inst() > 1 ? " (instance " + std::to_string((int)w.stage[1]) + ")" : "";
+    return fail((mps_status)code, std::string(where) + ": " + what + inst);
+  }
+  for (const auto& p : w.pending) std::memcpy(p.dst, w.stage + p.off, p.count * sizeof(double));
+  w.pending.clear();
+  return MPS_OK;
+}
+
+// theta (host or device; one row of n_theta values per instance) -> the workspace's per-instance
+// copy
+static mps_status stage_theta(mps_state* s, const double* theta, int n_theta, const double** d_theta) {
+  Workspace& w = *s->ws;
+  const Batch bt = s->batch();
+  if (n_theta < 0) return fail(MPS_EINVAL, "n_theta < 0");
+  if (n_theta > 0 && !theta) return fail(MPS_EINVAL, "theta is NULL");
+  MPS_TRY(w.theta.ensure(std::max(1, n_theta) * sizeof(double)));
+  *d_theta = w.theta.as<double>();
+  if (n_theta == 0) return MPS_OK;
+  const size_t row = (size_t)n_theta * sizeof(double);
+  if (is_device_ptr(theta)) {   // finiteness is checked by the gate-matrix kernel
+    launch_copy_f64(bt, w.theta.as<double>(), bt.stride, theta, row, n_theta, s->st);
+    return MPS_OK;
+  }
+  const size_t total = (size_t)n_theta * bt.n;
+  for (size_t i = 0; i < total; ++i)
+    if (!std::isfinite(theta[i])) return fail(MPS_EINVAL, "theta contains a non-finite value");
+  const size_t o = stage_take(w, total);
+  std::memcpy(w.stage + o, theta, total * sizeof(double));
+  launch_copy_f64(bt, w.theta.as<double>(), bt.stride, w.stage_dev + o, row, n_theta, s->st);
+  return MPS_OK;
+}
+
+// per-instance device result (count values) -> caller's array of one row per instance (device:
+// copy kernel; host: through the staging)
+static mps_status put_out(mps_state* s, double* dst, const double* dsrc, size_t count) {
   if (!dst || count == 0) return MPS_OK;
-  MPS_CU(cudaMemcpyAsync(dst, dsrc, count * sizeof(double),
-                         is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  Workspace& w = *s->ws;
+  const Batch bt = s->batch();
+  const size_t row = count * sizeof(double);
+  if (is_device_ptr(dst)) {
+    launch_copy_f64(bt, dst, row, dsrc, bt.stride, count, s->st);
+    return MPS_OK;
+  }
+  const size_t o = stage_take(w, count * bt.n);
+  launch_copy_f64(bt, w.stage_dev + o, row, dsrc, bt.stride, count, s->st);
+  w.pending.push_back({dst, o, count * bt.n});
   return MPS_OK;
 }
 
@@ -886,8 +972,8 @@ static mps_status ensure_gate_matrices(mps_state* s, const mps_circuit* c) {
 
 static void gate_matrices_launch(mps_state* s, const mps_circuit* c, const double* d_theta, int n_theta) {
   Workspace& w = *s->ws;
-  launch_gate_matrices(c->gates.p, c->n_gates, d_theta, n_theta, w.G.as<double2>(), w.dG.as<double2>(),
-                       s->status.as<int>(), s->st);
+  launch_gate_matrices(s->batch(), c->gates.p, c->n_gates, d_theta, n_theta, w.G.as<double2>(),
+                       w.dG.as<double2>(), s->status.as<int>(), s->st);
 }
 
 static mps_status gate_matrices(mps_state* s, const mps_circuit* c, const double* d_theta, int n_theta) {
@@ -916,31 +1002,55 @@ const char* mps_last_error(void) { return mpsi::g_err.c_str(); }
 
 int64_t mps_kernel_launches(void) { return (int64_t)mpsk::launches(); }
 
-mps_status mps_init_product(int32_t n_qubits, const uint8_t* bits, const mps_config* cfg, mps_state** out) {
+mps_status mps_init_product_batch(int32_t n_inst, int32_t n_qubits, const uint8_t* bits, const mps_config* cfg,
+                                  mps_state** out) {
   clear_error();
   if (!out) return fail(MPS_EINVAL, "mps_init_product: out is NULL");
+  if (n_inst < 1 || n_inst > 4096) return fail(MPS_EINVAL, "mps_init_product: n_inst must be in 1..4096");
   if (n_qubits < 2 || n_qubits > 64) return fail(MPS_EINVAL, "mps_init_product: n_qubits must be in 2..64");
   if (!bits) return fail(MPS_EINVAL, "mps_init_product: bits is NULL");
   MPS_TRY(validate_config(cfg));
-  for (int i = 0; i < n_qubits; ++i)
+  for (int i = 0; i < n_qubits * n_inst; ++i)
     if (bits[i] > 1) return fail(MPS_EINVAL, "mps_init_product: bits must be 0 or 1");
   std::unique_ptr<mps_state> s(new mps_state());
+  s->uid = next_uid();
   s->cfg = *cfg;   // checkpoint_every == 0: automatic (whole-circuit tape when it fits)
   s->st = (cudaStream_t)cfg->cuda_stream;
   s->L.build(n_qubits, cfg->max_bond);
-  s->ws.reset(new Workspace());
+  s->arena.reset(new Arena());
+  MPS_TRY(s->arena->init(n_inst));
+  s->buf.mem.arena = s->arena.get();
+  s->status.arena = s->arena.get();
+  s->ws.reset(new Workspace(s->arena.get()));
   MPS_TRY(s->buf.alloc(s->L));
   MPS_TRY(s->status.alloc(sizeof(int)));
   const Layout& L = s->L;
-  std::vector<double2> hB(L.site_elems(), make_double2(0.0, 0.0));
+  std::vector<double2> hB(L.site_elems());
   std::vector<double> hl(L.lam_elems(), 0.0);
   std::vector<int> hd(n_qubits + 1, 1);
-  for (int q = 0; q < n_qubits; ++q) hB[L.site_off[q] + bits[q]] = make_double2(1.0, 0.0);   // [1][2][1]
   for (int i = 0; i <= n_qubits; ++i) hl[L.lam_off[i]] = 1.0;
-  MPS_CU(cudaMemcpy(s->buf.B, hB.data(), hB.size() * sizeof(double2), cudaMemcpyHostToDevice));
-  MPS_CU(cudaMemcpy(s->buf.lam, hl.data(), hl.size() * sizeof(double), cudaMemcpyHostToDevice));
-  MPS_CU(cudaMemcpy(s->buf.dims, hd.data(), hd.size() * sizeof(int), cudaMemcpyHostToDevice));
+  for (int r = 0; r < n_inst; ++r) {
+    const size_t io = (size_t)r * s->arena->stride;
+    std::fill(hB.begin(), hB.end(), make_double2(0.0, 0.0));
+    for (int q = 0; q < n_qubits; ++q)   // [1][2][1]
+      hB[L.site_off[q] + bits[(size_t)r * n_qubits + q]] = make_double2(1.0, 0.0);
+    MPS_CU(cudaMemcpy(ish(s->buf.B, io), hB.data(), hB.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    MPS_CU(cudaMemcpy(ish(s->buf.lam, io), hl.data(), hl.size() * sizeof(double), cudaMemcpyHostToDevice));
+    MPS_CU(cudaMemcpy(ish(s->buf.dims, io), hd.data(), hd.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
+  MPS_TRY(legacy_fence());
   *out = s.release();
+  return MPS_OK;
+}
+
+mps_status mps_init_product(int32_t n_qubits, const uint8_t* bits, const mps_config* cfg, mps_state** out) {
+  return mps_init_product_batch(1, n_qubits, bits, cfg, out);
+}
+
+mps_status mps_state_instances(const mps_state* s, int32_t* n_inst) {
+  clear_error();
+  if (!s || !n_inst) return fail(MPS_EINVAL, "mps_state_instances: NULL argument");
+  *n_inst = s->n_inst();
   return MPS_OK;
 }
 
@@ -948,13 +1058,22 @@ mps_status mps_clone(const mps_state* s, mps_state** out) {
   clear_error();
   if (!s || !out) return fail(MPS_EINVAL, "mps_clone: NULL argument");
   std::unique_ptr<mps_state> c(new mps_state());
+  c->uid = next_uid();
   c->cfg = s->cfg;
   c->st = s->st;
   c->L = s->L;
-  c->ws.reset(new Workspace());
+  c->arena.reset(new Arena());
+  MPS_TRY(c->arena->init(s->n_inst()));
+  c->buf.mem.arena = c->arena.get();
+  c->status.arena = c->arena.get();
+  c->ws.reset(new Workspace(c->arena.get()));
   MPS_TRY(c->buf.alloc(c->L));
   MPS_TRY(c->status.alloc(sizeof(int)));
-  MPS_TRY(c->buf.copy_from(s->buf, s->L, s->st));
+  // instance i of the clone <- instance i of s (the two arenas have different strides)
+  const Batch bs = s->batch();
+  const Batch bc = c->batch();
+  launch_copy_f64(Batch{bs.n, 0}, c->buf.mem.as<double>(), bc.stride, s->buf.mem.as<double>(), bs.stride,
+                  c->buf.mem.bytes / sizeof(double), s->st);
   MPS_CU(cudaStreamSynchronize(s->st));
   *out = c.release();
   return MPS_OK;
@@ -974,10 +1093,15 @@ mps_status mps_profile_read(mps_state* s, double* out6) {
   if (!s || !out6) return fail(MPS_EINVAL, "mps_profile_read: NULL argument");
   Workspace& w = *s->ws;
   double fl[4] = {0.0, 0.0, 0.0, 0.0};
-  if (w.stats.p) {
+  if (w.stats.p) {   // summed over the instances
     MPS_CU(cudaStreamSynchronize(s->st));
-    MPS_CU(cudaMemcpy(fl, w.stats.p, sizeof(fl), cudaMemcpyDeviceToHost));
-    MPS_CU(cudaMemset(w.stats.p, 0, sizeof(fl)));
+    for (int i = 0; i < s->n_inst(); ++i) {
+      double* di = ish(w.stats.as<double>(), (size_t)i * s->arena->stride);
+      double fi[4];
+      MPS_CU(cudaMemcpy(fi, di, sizeof(fi), cudaMemcpyDeviceToHost));
+      MPS_CU(cudaMemset(di, 0, sizeof(fi)));
+      for (int q = 0; q < 4; ++q) fl[q] += fi[q];
+    }
   }
   out6[0] = w.svd_ms;
   out6[1] = (double)w.svd_launches;
@@ -998,17 +1122,30 @@ void mps_free(mps_state* s) {
 }
 
 mps_status mps_read_state(const mps_state* s, int32_t* dims, double* lam, double* tensors) {
+  return mps_read_state_instance(s, 0, dims, lam, tensors);
+}
+
+mps_status mps_read_state_instance(const mps_state* s, int32_t inst, int32_t* dims, double* lam,
+                                   double* tensors) {
   clear_error();
   if (!s || !dims) return fail(MPS_EINVAL, "mps_read_state: NULL argument");
+  if (inst < 0 || inst >= s->n_inst()) return fail(MPS_EINVAL, "mps_read_state: instance out of range");
   const Layout& L = s->L;
+  const size_t io = (size_t)inst * s->arena->stride;
+  struct {
+    const double2* B;
+    const double* lam;
+    const int* dims;
+  } view{ish(s->buf.B, io), ish(s->buf.lam, io), ish(s->buf.dims, io)};
+  const auto* sbp = &view;
   MPS_CU(cudaStreamSynchronize(s->st));
   std::vector<int> d(L.n + 1);
-  MPS_CU(cudaMemcpy(d.data(), s->buf.dims, (L.n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+  MPS_CU(cudaMemcpy(d.data(), sbp->dims, (L.n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
   std::memcpy(dims, d.data(), (L.n + 1) * sizeof(int));
   if (lam) {
     size_t o = 0;
     for (int i = 1; i < L.n; ++i) {
-      MPS_CU(cudaMemcpy(lam + o, s->buf.lam + L.lam_off[i], d[i] * sizeof(double), cudaMemcpyDeviceToHost));
+      MPS_CU(cudaMemcpy(lam + o, sbp->lam + L.lam_off[i], d[i] * sizeof(double), cudaMemcpyDeviceToHost));
       o += d[i];
     }
   }
@@ -1016,7 +1153,7 @@ mps_status mps_read_state(const mps_state* s, int32_t* dims, double* lam, double
     size_t o = 0;
     for (int q = 0; q < L.n; ++q) {
       size_t e = (size_t)d[q] * 2 * d[q + 1];
-      MPS_CU(cudaMemcpy(tensors + 2 * o, s->buf.B + L.site_off[q], e * sizeof(double2), cudaMemcpyDeviceToHost));
+      MPS_CU(cudaMemcpy(tensors + 2 * o, sbp->B + L.site_off[q], e * sizeof(double2), cudaMemcpyDeviceToHost));
       o += e;
     }
   }
@@ -1070,6 +1207,7 @@ mps_status mps_circuit_create(int32_t n_qubits, const mps_gate* gates, int32_t n
     MPS_CU(cudaMemcpy(c->csr_gate.p, gi.data(), gi.size() * sizeof(int), cudaMemcpyHostToDevice));
     MPS_CU(cudaMemcpy(c->csr_scale.p, sc.data(), sc.size() * sizeof(double), cudaMemcpyHostToDevice));
   }
+  MPS_TRY(legacy_fence());
   *out = c.release();
   return MPS_OK;
 }
@@ -1120,6 +1258,7 @@ mps_status mps_hamiltonian_create(int32_t n_qubits, const mps_hamiltonian* hin, 
   MPS_TRY(h->d_coeff.alloc(std::max<size_t>(1, h->c.size()) * sizeof(double)));
   if (!h->c.empty())
     MPS_CU(cudaMemcpy(h->d_coeff.p, h->c.data(), h->c.size() * sizeof(double), cudaMemcpyHostToDevice));
+  MPS_TRY(legacy_fence());
   *out = h.release();
   return MPS_OK;
 }
@@ -1130,14 +1269,15 @@ mps_status mps_apply_circuit_dev(mps_state* s, const mps_circuit* c, const doubl
   clear_error();
   if (!s) return fail(MPS_EINVAL, "mps_apply_circuit: state is NULL");
   MPS_TRY(check_circuit(s, c, n_theta));
+  MPS_TRY(begin_call(s, std::max(0, n_theta)));
   const double* d_theta = nullptr;
   MPS_TRY(stage_theta(s, theta, n_theta, &d_theta));
   MPS_TRY(ensure_forward_scratch(s->L, *s->ws));
   MPS_TRY(gate_matrices(s, c, d_theta, n_theta));
   s->ws->ev_used = 0;
-  Ctx cx{&s->L, &s->cfg, s->st, s->status.as<int>(), s->ws.get()};
+  Ctx cx{&s->L, &s->cfg, s->st, s->status.as<int>(), s->ws.get(), s->batch()};
   MPS_TRY(forward_gates(cx, s->buf, c, s->ws->G.as<double2>(), 0, c->n_gates, nullptr));
-  MPS_TRY(check_status_word(s->st, s->status, "mps_apply_circuit"));
+  MPS_TRY(finish_call(s, "mps_apply_circuit"));
   return harvest_profile(*s->ws);
 }
 
@@ -1158,14 +1298,15 @@ mps_status mps_energy_dev(const mps_state* s, const mps_hamiltonian_dev* h, doub
   mps_state* ms = const_cast<mps_state*>(s);
   Workspace& w = *ms->ws;
   const int nt = (int)h->x.size();
+  MPS_TRY(begin_call(ms, 1 + (size_t)nt));
   MPS_TRY(w.scalars.ensure((2 + std::max(1, nt)) * sizeof(double)));
   double* dE = w.scalars.as<double>();
   double* dX = expect_out ? dE + 2 : nullptr;
   MPS_TRY(energy_pass_impl(s->L, s->buf, s->st, ms->status.as<int>(), const_cast<mps_hamiltonian_dev*>(h), dE, dX,
                            nullptr));
-  MPS_TRY(put_out(E_out, dE, 1, s->st));
-  MPS_TRY(put_out(expect_out, dX, nt, s->st));
-  return check_status_word(s->st, ms->status, "mps_energy");
+  MPS_TRY(put_out(ms, E_out, dE, 1));
+  MPS_TRY(put_out(ms, expect_out, dX, nt));
+  return finish_call(ms, "mps_energy");
 }
 
 mps_status mps_energy_cotangent_dev(const mps_state* s, const mps_hamiltonian_dev* h, double* E_out,
@@ -1176,24 +1317,25 @@ mps_status mps_energy_cotangent_dev(const mps_state* s, const mps_hamiltonian_de
   mps_state* ms = const_cast<mps_state*>(s);
   Workspace& w = *ms->ws;
   const Layout& L = s->L;
+  MPS_TRY(begin_call(ms, 1));
   MPS_TRY(w.scalars.ensure(4 * sizeof(double)));
   MPS_TRY(w.Bbar.ensure(L.site_elems() * sizeof(double2)));
   double* dE = w.scalars.as<double>();
   MPS_TRY(energy_pass_impl(L, s->buf, s->st, ms->status.as<int>(), const_cast<mps_hamiltonian_dev*>(h), dE, nullptr,
                            w.Bbar.as<double2>()));
-  MPS_TRY(check_status_word(s->st, ms->status, "mps_energy_cotangent"));
+  MPS_TRY(put_out(ms, E_out, dE, 1));
+  MPS_TRY(finish_call(ms, "mps_energy_cotangent"));
+  // dE/dB* of instance 0
   std::vector<int> d(L.n + 1);
   MPS_CU(cudaMemcpy(d.data(), s->buf.dims, (L.n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
   const bool dev = is_device_ptr(Bbar_out);
   size_t o = 0;
   for (int q = 0; q < L.n; ++q) {
     size_t e = (size_t)d[q] * 2 * d[q + 1];
-    MPS_CU(cudaMemcpyAsync(Bbar_out + 2 * o, w.Bbar.as<double2>() + L.site_off[q], e * sizeof(double2),
-                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->st));
+    MPS_CU(cudaMemcpy(Bbar_out + 2 * o, w.Bbar.as<double2>() + L.site_off[q], e * sizeof(double2),
+                      dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
     o += e;
   }
-  MPS_TRY(put_out(E_out, dE, 1, s->st));
-  MPS_CU(cudaStreamSynchronize(s->st));
   return MPS_OK;
 }
 
@@ -1255,7 +1397,7 @@ mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, doub
   a.lam_left = one;
   a.lam_left_copy = nullptr;
   a.status = status.as<int>();
-  launch_svd(a, m, ncol, 0);
+  launch_svd(Batch{1, 0}, a, m, ncol, 0);
   MPS_CU(cudaGetLastError());
   MPS_CU(cudaDeviceSynchronize());
   int code = 0, k = 0;
@@ -1303,6 +1445,7 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
   MPS_TRY(check_circuit(s, c, n_theta));
   const Layout& L = s->L;
   Workspace& w = *s->ws;
+  MPS_TRY(begin_call(s, 1 + 2 * (size_t)std::max(0, n_theta) + (gate_grad_out ? (size_t)c->n_gates : 0)));
   const double* d_theta = nullptr;
   MPS_TRY(stage_theta(s, theta, n_theta, &d_theta));
   MPS_TRY(ensure_forward_scratch(L, w));
@@ -1323,12 +1466,17 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
     return align256(cp * sizeof(double2)) + align256(db * sizeof(double));
   };
   int K = s->cfg.checkpoint_every;
-  if (K <= 0) {   // automatic: keep the tape of the whole circuit when it takes < 40% of free memory
+  if (K <= 0 && w.auto_uid == c->uid) {
+    K = w.auto_K;   // decided on the first call with this circuit
+  } else if (K <= 0) {   // automatic: keep the whole circuit's tape when it takes < 40% of free memory
     size_t all = 0;
     for (int t = 0; t < ng; ++t) all += slot_bytes(c->host[t].bond);
     size_t fr = 0, tot = 0;
     MPS_CU(cudaMemGetInfo(&fr, &tot));
-    K = (all + w.tape.bytes <= (size_t)(0.4 * (double)(fr + w.tape.bytes))) ? std::max(1, ng) : 512;
+    const double ni = (double)s->n_inst();
+    K = (ni * (double)(all + w.tape.bytes) <= 0.4 * ((double)fr + ni * (double)w.tape.bytes)) ? std::max(1, ng) : 512;
+    w.auto_uid = c->uid;
+    w.auto_K = K;
   }
   const int nseg = (ng + K - 1) / K;
   if (!w.work_ok) {
@@ -1338,7 +1486,7 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
   }
   if (nseg > 1)
     while ((int)w.snaps.size() < nseg) {
-      w.snaps.emplace_back(new StateBuf());
+      w.snaps.emplace_back(new StateBuf(w.arena));
       MPS_TRY(w.snaps.back()->alloc(L));
     }
   // tape arena for the largest segment
@@ -1369,7 +1517,7 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
   MPS_TRY(w.gate_grad.ensure(std::max(1, ng) * sizeof(double)));
   MPS_TRY(w.grad.ensure(std::max(1, n_theta) * sizeof(double)));
   MPS_TRY(w.scalars.ensure(4 * sizeof(double)));
-  Ctx cx{&L, &s->cfg, s->st, s->status.as<int>(), &w};
+  Ctx cx{&L, &s->cfg, s->st, s->status.as<int>(), &w, s->batch()};
   const double2* G = w.G.as<double2>();
   const double2* dG = w.dG.as<double2>();
   double* dE = w.scalars.as<double>();
@@ -1416,8 +1564,8 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
     }
     // energy and its cotangent
     MPS_TRY(energy_pass_impl(L, w.work, s->st, s->status.as<int>(), h, dE, nullptr, w.Bbar.as<double2>()));
-    MPS_CU(cudaMemsetAsync(w.lambar.p, 0, L.lam_elems() * sizeof(double), s->st));
-    MPS_CU(cudaMemsetAsync(w.gate_grad.p, 0, std::max(1, ng) * sizeof(double), s->st));
+    launch_zero_f64(cx.bt, w.lambar.as<double>(), L.lam_elems(), s->st);
+    launch_zero_f64(cx.bt, w.gate_grad.as<double>(), std::max(1, ng), s->st);
     // reverse, segment by segment (re-running a segment's forward from its snapshot with a tape)
     for (int seg = nseg - 1; seg >= 0; --seg) {
       const int g0 = seg * K, g1 = std::min(ng, (seg + 1) * K);
@@ -1432,15 +1580,16 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
       MPS_CU(cudaGetLastError());
     }
     if (n_theta > 0) {
-      MPS_CU(cudaMemsetAsync(w.grad.p, 0, n_theta * sizeof(double), s->st));
-      launch_theta_reduce(w.gate_grad.as<double>(), c->csr_off.as<int>(), c->csr_gate.as<int>(),
+      launch_zero_f64(cx.bt, w.grad.as<double>(), n_theta, s->st);
+      launch_theta_reduce(cx.bt, w.gate_grad.as<double>(), c->csr_off.as<int>(), c->csr_gate.as<int>(),
                           c->csr_scale.as<double>(), c->max_theta_idx + 1, w.grad.as<double>(), s->st);
     }
     return MPS_OK;
   };
   // The graph is valid while none of the buffers it touches has moved.
   const EnergyCache* ec = h->cache.get();
-  std::vector<const void*> key = {(const void*)c->uid, (const void*)h->uid, (const void*)(intptr_t)n_theta,
+  std::vector<const void*> key = {(const void*)s->arena->uid, (const void*)c->uid, (const void*)h->uid,
+                                  (const void*)(intptr_t)n_theta,
                                   (const void*)(intptr_t)K, w.tape.p, w.rv.p, w.Bbar.p, w.lambar.p,
                                   w.gate_grad.p, w.grad.p, w.theta.p, w.G.p, w.dG.p, w.A.p, w.svd.p, w.C.p,
                                   w.Vs.p, w.s.p, w.stats.p, w.scalars.p, w.work.mem.p, w.rec.mem.p,
@@ -1481,10 +1630,10 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
     MPS_TRY(body());
     w.graph_seen = key;
   }
-  MPS_TRY(put_out(E_out, dE, 1, s->st));
-  MPS_TRY(put_out(grad_out, w.grad.as<double>(), n_theta, s->st));
-  MPS_TRY(put_out(gate_grad_out, w.gate_grad.as<double>(), ng, s->st));
-  MPS_TRY(check_status_word(s->st, s->status, "mps_energy_grad"));
+  MPS_TRY(put_out(s, E_out, dE, 1));
+  MPS_TRY(put_out(s, grad_out, w.grad.as<double>(), n_theta));
+  MPS_TRY(put_out(s, gate_grad_out, w.gate_grad.as<double>(), ng));
+  MPS_TRY(finish_call(s, "mps_energy_grad"));
   return harvest_profile(w);
 }
 

@@ -152,7 +152,7 @@ extern "C" mps_status mps_svd_noalloc(int32_t m, int32_t ncol, const double* A, 
   a.lam_left_copy = nullptr;
   a.status = v.status;
   a.stats = nullptr;
-  launch_svd(a, m, ncol, stream);
+  launch_svd(Batch{1, 0}, a, m, ncol, stream);
   const int K = m < ncol ? m : ncol;
   const int outs = (ncol > m ? ncol : m) * K;
   na_finish<<<(outs + 255) / 256, 256, 0, stream>>>(v, m, ncol, s_out, reinterpret_cast<double2*>(V_out),

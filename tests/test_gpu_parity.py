@@ -284,3 +284,98 @@ def test_string_shards_sum_to_the_full_cotangent_on_gpu(M):
         B_sum = Br if B_sum is None else [a + b for a, b in zip(B_sum, Br)]
     assert abs(E_sum - E) < 1e-12
     assert max(np.abs(a - b).max() for a, b in zip(B_sum, Bbar)) < 1e-12
+
+
+# ---- batched instances: one launch per kernel serves every instance ------------------------------
+
+def _batch_case(case):
+    if case == "cfg0":
+        return S.make_problem(0), None, None, None, 0
+    if case == "n8_trunc":
+        p = small(D=4, eps=1e-10)
+        return p, p.excitations[:12], 4, 1e-10, 5           # truncation + checkpoint segments
+    p = S.make_problem(1)
+    return p, p.excitations[:12], None, None, 0
+
+
+@pytest.mark.parametrize("case", ["cfg0", "n8_trunc", "cfg1_prefix"])
+def test_batched_instances_equal_single_instance_runs_bit_for_bit(M, case):
+    """Every instance of a batched state gives exactly the bits of its own single-instance run,
+    and matches the oracle."""
+    p, excs, D, eps, K = _batch_case(case)
+    excs = p.excitations if excs is None else excs
+    D = p.spec.D if D is None else D
+    eps = p.spec.eps if eps is None else eps
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    circ = M.Circuit(p.n, M.compile_excitations(p.n, excs))
+    ham = M.Hamiltonian(p.n, x, z, c)
+    rng = np.random.default_rng(7)
+    n_inst = 3
+    th = np.stack([p.theta[: len(excs)]] + [rng.uniform(-np.pi, np.pi, len(excs)) for _ in range(n_inst - 1)])
+    bits = np.stack([p.bits] * n_inst)
+    stb = M.State.product_batch(bits, D, eps, checkpoint_every=K)
+    E_b, g_b, gg_b = M.energy_grad(stb, circ, th, ham, gate_grad=True)
+    assert E_b.shape == (n_inst,) and g_b.shape == (n_inst, len(excs))
+    og = ansatz.compile_circuit(p.n, excs)
+    oh = pauli.jw_hamiltonian(p.h, p.eri)
+    for i in range(n_inst):
+        st1 = M.State.product(p.bits, D, eps, checkpoint_every=K)
+        E1, g1, gg1 = M.energy_grad(st1, circ, th[i], ham, gate_grad=True)
+        assert E_b[i] == E1 and np.array_equal(g_b[i], g1) and np.array_equal(gg_b[i], gg1)
+        if i < 2:
+            r = OM.energy_grad(OM.init_product(p.bits), og, th[i], oh, D, eps, checkpoint_every=512)
+            assert abs(E_b[i] - r.E) <= E_TOL * max(1.0, abs(r.E))
+            assert np.linalg.norm(g_b[i] - r.grad) <= G_TOL * max(1.0, np.linalg.norm(r.grad))
+    # the state itself is untouched; each instance is readable
+    for i in range(n_inst):
+        dims, _, _ = stb.read(i)
+        assert list(dims) == [1] * (p.n + 1)
+
+
+def test_batched_forward_state_and_energy_per_instance(M):
+    p = small()
+    excs = p.excitations
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    circ = M.Circuit(p.n, M.compile_excitations(p.n, excs))
+    ham = M.Hamiltonian(p.n, x, z, c)
+    rng = np.random.default_rng(11)
+    th = rng.uniform(-np.pi, np.pi, (4, len(excs)))
+    bits = np.stack([p.bits, p.bits[::-1], p.bits, p.bits])     # instances may start from different states
+    stb = M.State.product_batch(bits, p.spec.D, p.spec.eps)
+    M.apply_circuit(stb, circ, th)
+    E_b, ex_b = M.energy(stb, ham, expect=True)
+    og = ansatz.compile_circuit(p.n, excs)
+    oh = pauli.jw_hamiltonian(p.h, p.eri)
+    for i in range(4):
+        dims, lams, B = stb.read(i)
+        ref = OM.apply_circuit(OM.init_product(bits[i]), og, th[i], p.spec.D, p.spec.eps)
+        assert list(dims[1:-1]) == ref.bond_dims()
+        assert np.abs(OM.to_dense(OM.MPS(B, lams)) - OM.to_dense(ref)).max() < 1e-10
+        Er = OM.energy(ref, oh)
+        assert abs(E_b[i] - Er) <= E_TOL * max(1.0, abs(Er))
+
+
+def test_batched_device_outputs_and_instance_error(M):
+    import torch
+    p = S.make_problem(0)
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    circ = M.Circuit(p.n, M.compile_excitations(p.n, p.excitations))
+    ham = M.Hamiltonian(p.n, x, z, c)
+    n_inst = 5
+    th = np.stack([p.theta + 0.1 * i for i in range(n_inst)])
+    stb = M.State.product_batch(np.stack([p.bits] * n_inst), p.spec.D, p.spec.eps)
+    E_h, g_h = M.energy_grad(stb, circ, th, ham)
+    th_d = torch.tensor(th, device="cuda")
+    E_d = torch.zeros(n_inst, dtype=torch.float64, device="cuda")
+    g_d = torch.zeros((n_inst, th.shape[1]), dtype=torch.float64, device="cuda")
+    M.energy_grad(stb, circ, th_d, ham, out=(E_d, g_d))
+    assert np.array_equal(E_d.cpu().numpy(), E_h) and np.array_equal(g_d.cpu().numpy(), g_h)
+    # a non-finite angle in one instance (device input: caught by the gate-matrix kernel)
+    bad = th_d.clone()
+    bad[3, 1] = float("nan")
+    with pytest.raises(M.api._lib.MpsError) as ei:
+        M.energy_grad(stb, circ, bad, ham, out=(E_d, g_d))
+    assert ei.value.code == 1 and "instance 3" in str(ei.value)
+    # the state recovers: the next call is clean
+    E2, g2 = M.energy_grad(stb, circ, th, ham)
+    assert np.array_equal(E2, E_h) and np.array_equal(g2, g_h)
