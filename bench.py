@@ -3,8 +3,10 @@
 
 One step = one full evaluation of E(theta) and dE/dtheta (forward gates with truncated SVDs,
 trie-shared Pauli sweeps, energy cotangent, exact reverse pass) for each of B independent
-instances of the workload, the instances running concurrently (one CUDA stream and one host
-thread each).  `value` = instances x steps / device time of the timed steps, summed over ranks.
+instances of the workload.  The instances live in one batched state: every kernel launch of
+the evaluation serves all B of them (the gate SVD runs one CTA per instance, so B = 152 fills
+the GPU), on one stream, replayed as one CUDA graph.  `value` = instances / device time of a
+step, summed over ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--instances B] [--impl ours|reference]
 
@@ -20,16 +22,12 @@ import os
 import statistics
 import subprocess
 import sys
-import threading
 import time
 
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
-# one hardware work queue per concurrent instance stream (the runtime default is 8, which makes
-# streams beyond the eighth share queues and wait on each other)
-os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import synthetic as S  # noqa: E402
 
@@ -38,6 +36,9 @@ WORKLOADS = {
     # name: (config, excitation prefix or None)
     "n12_D64": (1, None),
     "n4_D16": (0, None),
+    # prefixes of the n12_D64 circuit (same shapes; used for profiler captures)
+    "n12_D64_p10": (1, 10),
+    "n12_D64_p40": (1, 40),
 }
 # Per-SM ALU peaks used for the single-CTA SVD kernel (recipe nominal figures, per SM):
 # FP64 1.25 TFLOP/s / 152 SMs; FP32 152 SMs x 128 FMA/clk x 2 x 2.07 GHz = 80.5 TFLOP/s / 152.
@@ -51,10 +52,11 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--instances", type=int, default=32)
+    ap.add_argument("--instances", type=int, default=152)
     ap.add_argument("--workload", default="n12_D64", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
@@ -172,45 +174,22 @@ def run_ours(args, rank, world, local):
     x, z, c = M.build_hamiltonian(p.h, p.eri)
     gates = M.compile_excitations(p.n, excs)
     circ = M.Circuit(p.n, gates)
+    ham = M.Hamiltonian(p.n, x, z, c)
     B = args.instances
     n_theta = len(excs)
-    streams = [torch.cuda.Stream() for _ in range(B)]
-    states = [M.State.product(p.bits, p.spec.D, p.spec.eps, checkpoint_every=0, stream=streams[i])
-              for i in range(B)]
-    hams = [M.Hamiltonian(p.n, x, z, c) for _ in range(B)]
+    stream = torch.cuda.Stream()
+    state = M.State.product_batch(np.stack([p.bits] * B), p.spec.D, p.spec.eps, checkpoint_every=0,
+                                  stream=stream)
     # per-instance angles: the workload's theta for instance 0, fresh seeded angles for the others
-    thetas_h = [np.ascontiguousarray(p.theta[:n_theta] if i == 0 else
-                                     S.random_theta(S.seed_for(1, 500 + 1000 * rank + i), n_theta)) for i in range(B)]
-    thetas_d = [torch.tensor(t, dtype=torch.float64, device="cuda") for t in thetas_h]
-    outs_d = [(torch.zeros(1, dtype=torch.float64, device="cuda"),
-               torch.zeros(n_theta, dtype=torch.float64, device="cuda")) for _ in range(B)]
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > L2
-    errors = []
-
-    def one_step(device_io: bool):
-        """All B instances concurrently; returns wall seconds (host clock)."""
-        barrier = threading.Barrier(B)
-
-        def worker(i):
-            try:
-                barrier.wait()
-                with torch.cuda.stream(streams[i]):
-                    if device_io:
-                        M.energy_grad(states[i], circ, thetas_d[i], hams[i], out=outs_d[i])
-                    else:
-                        M.energy_grad(states[i], circ, thetas_h[i], hams[i])
-            except Exception as e:  # noqa: BLE001
-                errors.append(repr(e))
-
-        th = [threading.Thread(target=worker, args=(i,)) for i in range(B)]
-        t0 = time.perf_counter()
-        for t in th:
-            t.start()
-        for t in th:
-            t.join()
-        if errors:
-            raise RuntimeError(errors[0])
-        return time.perf_counter() - t0
+    thetas_h = np.ascontiguousarray(np.stack(
+        [p.theta[:n_theta] if i == 0 else S.random_theta(S.seed_for(1, 500 + 1000 * rank + i), n_theta)
+         for i in range(B)]))
+    with torch.cuda.stream(stream):
+        thetas_d = torch.tensor(thetas_h, dtype=torch.float64, device="cuda")
+        E_d = torch.zeros(B, dtype=torch.float64, device="cuda")
+        g_d = torch.zeros((B, n_theta), dtype=torch.float64, device="cuda")
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > L2
+    torch.cuda.synchronize()
 
     def sync_all():
         torch.cuda.synchronize()
@@ -219,40 +198,32 @@ def run_ours(args, rank, world, local):
             dist.barrier()
             torch.cuda.synchronize()
 
-    # warm-up: the first call of each instance runs eagerly, the second captures a CUDA graph
-    # of the whole evaluation, later calls replay it
+    # SVD launches are bracketed by CUDA events on the state's stream (captured into the graph)
+    state.profile(True)
+    # warm-up: the first call runs eagerly, the second captures the whole evaluation as a CUDA
+    # graph, later calls replay it
     for _ in range(args.warmup):
-        one_step(True)
-    for st in states:
-        st.profile_read()          # reset the device-side SVD counters
+        M.energy_grad(state, circ, thetas_d, ham, out=(E_d, g_d))
+    state.profile_read()          # reset the counters
     clocks = ClockSampler(local)
     launches0 = M.kernel_launches()
     sync_all()
     clocks.start()
     dev_ms = 0.0
     for _ in range(args.steps):
-        flush.fill_(1.0)                       # L2 flush between timed steps
-        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)                   # L2 flush between timed steps
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        ends = []
-        for s in streams:
-            s.wait_event(e0)
-        one_step(True)
-        for s in streams:
-            ev = torch.cuda.Event()
-            ev.record(s)
-            ends.append(ev)
-        for ev in ends:
-            torch.cuda.current_stream().wait_event(ev)
-        e1.record()
-        torch.cuda.synchronize()
+        e0.record(stream)
+        M.energy_grad(state, circ, thetas_d, ham, out=(E_d, g_d))
+        e1.record(stream)
+        e1.synchronize()
         dev_ms += e0.elapsed_time(e1)
     sync_all()
     clk = clocks.stop()
     launches = M.kernel_launches() - launches0
-    prof = [st.profile_read() for st in states]
+    prof = state.profile_read()
     t_step = dev_ms / 1e3 / args.steps
     if world > 1:
         import torch.distributed as dist
@@ -264,7 +235,11 @@ def run_ours(args, rank, world, local):
     e2e = None
     if not args.no_e2e:
         sync_all()
-        walls = [one_step(False) for _ in range(max(1, min(args.steps, 1)))]
+        walls = []
+        for _ in range(max(1, min(args.steps, 2))):
+            t0 = time.perf_counter()
+            M.energy_grad(state, circ, thetas_h, ham)
+            walls.append(time.perf_counter() - t0)
         t_e2e = sum(walls) / len(walls)
         if world > 1:
             import torch.distributed as dist
@@ -273,45 +248,51 @@ def run_ours(args, rank, world, local):
             t_e2e = float(tt.item())
         e2e = {"value": B * world / t_e2e, "unit": "evals/s", "h2d_bytes_per_step": 8 * n_theta * B,
                "d2h_bytes_per_step": 8 * (1 + n_theta) * B}
-    # ---- cross-check of the per-launch SVD time with CUDA events (one untimed eager step) ----
-    states[0].profile(True)
-    states[0].profile_read()
-    M.energy_grad(states[0], circ, thetas_d[0], hams[0], out=outs_d[0])
-    ev = states[0].profile_read()
-    states[0].profile(False)
-    ev_ms_per_launch = ev["svd_ms"] / max(1, ev["svd_launches"])
-    # ---- roofline of the dominant kernel (the gate SVD, one CTA per matrix) ----
-    svd_ms = sum(q["svd_ms_device"] for q in prof)
-    n_svd = sum(q["svd_launches_device"] for q in prof)
-    f64 = sum(q["fp64_flops"] for q in prof)
-    f32 = sum(q["fp32_flops"] for q in prof)
+    # ---- Pauli-term expectations per second on the final states (energy pass alone) ----
+    st_f = state.clone()
+    M.apply_circuit(st_f, circ, thetas_d)
+    M.energy(st_f, ham)                                  # builds the sweep plan
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_rep = 3
+    for _ in range(n_rep):
+        M.energy(st_f, ham)
+    t_energy = (time.perf_counter() - t0) / n_rep
+    terms_per_s = len(x) * B / t_energy
+    st_f.free()
+    # ---- roofline of the dominant kernel (the gate SVD: one CTA per instance per launch) ----
     roof = None
-    if n_svd:
-        t_launch = svd_ms / 1e3 / n_svd
-        f64_l, f32_l = f64 / n_svd, f32 / n_svd
-        achieved = (f64_l + f32_l * P64_SM / P32_SM) / t_launch      # FP64-equivalent rate of one CTA
-        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": P64_SM / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / P64_SM, "traffic": None,
-                "kernel": "svd_kernel (gate SVD, one CTA = one SM per matrix)",
+    n_launch = prof["svd_launches"]
+    if n_launch:
+        t_launch = prof["svd_ms"] / 1e3 / n_launch                   # CUDA events, timed region
+        f64_l, f32_l = prof["fp64_flops"] / n_launch, prof["fp32_flops"] / n_launch
+        achieved = (f64_l + f32_l * P64_SM / P32_SM) / t_launch       # FP64-equivalent rate
+        peak = P64_SM * N_SM
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": f"svd_kernel (gate SVD; {B} CTAs per launch, one per instance)",
                 "per_launch": {"ms": 1e3 * t_launch, "fp64_flops": f64_l, "fp32_flops": f32_l,
-                               "launches": n_svd},
-                "note": "achieved = (F64 + F32*P64/P32) per launch / launch time (kernel's own %globaltimer "
-                        "over the timed steps; CUDA-event time per launch in an eager step: "
-                        f"{ev_ms_per_launch:.3f} ms); peak = recipe nominal FP64 1.25 TFLOP/s / 152 SMs "
-                        "(fallback; FP64 not in the measured peaks); FP32 per SM 128 FMA/clk x 2 x 2.07 GHz",
-                "svd_share_of_device_time": svd_ms / 1e3 / (t_step * args.steps * B)}
+                               "launches": n_launch},
+                "note": "achieved = (F64 + F32*P64/P32) flops per launch, counted on the device, / the "
+                        "launch's CUDA-event duration on the state's stream over the timed steps; peak = "
+                        "recipe nominal FP64 1.25 TFLOP/s for the GPU (fallback: FP64 is not in the measured "
+                        "peaks); FP32 converted at 152 SMs x 128 FMA/clk x 2 x 2.07 GHz",
+                "svd_share_of_step": prof["svd_ms"] / 1e3 / (t_step * args.steps)}
     if rank == 0:
-        cpu = oracle_sample(cfg)
+        cpu = None if args.no_cpu_baseline else oracle_sample(cfg)
         line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"{args.workload}: n={p.n} qubits, {p.spec.n_e} electrons, D={p.spec.D}, "
                                        f"eps={p.spec.eps}, {n_theta} theta, {len(gates)} gates, {len(x)} Pauli "
-                                       f"strings; {B} concurrent instances per GPU",
+                                       f"strings; {B} instances per GPU batched into every launch",
                            "instances_per_gpu": B, "l2": "512 MB buffer written between timed steps; "
-                                                         "per-instance tape ~GBs > L2",
+                                                         "per-instance tape ~0.9 GB > L2",
                            "precision": "FP64 contractions; SVD FP32-preconditioned, FP64-finished"},
-                "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk}
+                "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+                "pauli_terms_per_s": {"value": terms_per_s, "unit": "Pauli-term expectations/s",
+                                      "note": f"energy pass alone on the {B} final states "
+                                              f"({len(x)} strings each), host clock over {n_rep} calls"}}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

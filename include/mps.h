@@ -61,7 +61,7 @@ typedef struct {
   int32_t precision;         /* MPS_PRECISION_FP64 (only value accepted by this build) */
   int32_t checkpoint_every;  /* reverse pass: MPS snapshot every k gates, the segment
                                 re-run with a tape; 0 = automatic: one tape for the whole
-                                circuit when it fits in 40% of free device memory, else 512 */
+                                circuit when it fits in 60% of free device memory, else 512 */
   void* cuda_stream;         /* cudaStream_t, NULL = default stream */
 } mps_config;
 
@@ -261,9 +261,11 @@ mps_status mps_svd_noalloc(int32_t m, int32_t ncol, const double* A, int32_t D, 
  * floating-point operations its sweeps actually performed to a device counter.
  * mps_profile_read fills out6 = {SVD time in ms from the CUDA events, SVD launches timed by
  * events, FP64 flops, FP32 flops, SVD time in ms from the kernel's own %globaltimer reads, SVD
- * launches counted on the device} since the last read and resets them.  The flop and device-time
- * counters run whether or not profiling is enabled (also inside captured graphs); the events only
- * while it is enabled (calls then run without graph replay).  No counterpart in the paper.
+ * launches counted on the device} since the last read and resets them; counters are summed over
+ * the instances (one launch serves every instance, and its %globaltimer time is summed over its
+ * CTAs).  The flop and device-time counters run whether or not profiling is enabled; the events
+ * only while it is enabled.  Both work inside captured graphs (the events are recorded as
+ * external event nodes).  No counterpart in the paper.
  */
 mps_status mps_profile(mps_state* s, int32_t enable);
 mps_status mps_profile_read(mps_state* s, double* out6);

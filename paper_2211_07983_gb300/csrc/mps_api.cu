@@ -162,6 +162,7 @@ struct Workspace {
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<const void*> graph_key, graph_seen;
   long long graph_kernels = 0;
+  size_t graph_ev_used = 0;       // profiling events recorded by the captured graph
   // Host inputs and outputs of a call pass through pinned host memory that kernels read and
   // write directly (slot 0 receives the status word).  No call queues work on a copy engine:
   // copy-engine queues are shared by all streams, so an output copy that waits for one
@@ -228,6 +229,18 @@ static GemmDesc make_desc(const int* dims, const double2* A, int opA, const doub
   return d;
 }
 
+// Profiling event on the stream; under stream capture it is recorded as an external event node,
+// so that replays of the captured graph re-record it.
+static mps_status record_profile_event(cudaEvent_t e, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  MPS_CU(cudaStreamIsCapturing(st, &cs));
+  if (cs == cudaStreamCaptureStatusActive)
+    MPS_CU(cudaEventRecordWithFlags(e, st, cudaEventRecordExternal));
+  else
+    MPS_CU(cudaEventRecord(e, st));
+  return MPS_OK;
+}
+
 // one gate on bond b: contract -> SVD/truncate -> update (Sec. 3); with a tape when `tp`
 static mps_status forward_gate(Ctx& cx, StateBuf& sb, int b, const double2* Gt, const TapeSlot* tp) {
   const Layout& L = *cx.L;
@@ -263,11 +276,11 @@ static mps_status forward_gate(Ctx& cx, StateBuf& sb, int b, const double2* Gt, 
         w.ev_pool.push_back(e);
       }
     }
-    MPS_CU(cudaEventRecord(w.ev_pool[w.ev_used], cx.st));
+    MPS_TRY(record_profile_event(w.ev_pool[w.ev_used], cx.st));
   }
   launch_svd(cx.bt, a, 2 * L.cap[b], 2 * L.cap[b + 2], cx.st);
   if (w.profile) {
-    MPS_CU(cudaEventRecord(w.ev_pool[w.ev_used + 1], cx.st));
+    MPS_TRY(record_profile_event(w.ev_pool[w.ev_used + 1], cx.st));
     w.ev_used += 2;
   }
   GemmBatch g{};
@@ -1468,13 +1481,13 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
   int K = s->cfg.checkpoint_every;
   if (K <= 0 && w.auto_uid == c->uid) {
     K = w.auto_K;   // decided on the first call with this circuit
-  } else if (K <= 0) {   // automatic: keep the whole circuit's tape when it takes < 40% of free memory
+  } else if (K <= 0) {   // automatic: keep the whole circuit's tape when it takes < 60% of free memory
     size_t all = 0;
     for (int t = 0; t < ng; ++t) all += slot_bytes(c->host[t].bond);
     size_t fr = 0, tot = 0;
     MPS_CU(cudaMemGetInfo(&fr, &tot));
     const double ni = (double)s->n_inst();
-    K = (ni * (double)(all + w.tape.bytes) <= 0.4 * ((double)fr + ni * (double)w.tape.bytes)) ? std::max(1, ng) : 512;
+    K = (ni * (double)(all + w.tape.bytes) <= 0.6 * ((double)fr + ni * (double)w.tape.bytes)) ? std::max(1, ng) : 512;
     w.auto_uid = c->uid;
     w.auto_K = K;
   }
@@ -1599,7 +1612,8 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
   if (w.graph_exec && key == w.graph_key) {
     MPS_CU(cudaGraphLaunch(w.graph_exec, s->st));
     add_launches(w.graph_kernels);
-  } else if (!w.profile && key == w.graph_seen && s->cfg.cuda_stream != nullptr) {
+    w.ev_used = w.graph_ev_used;   // the graph re-records the profiling events of its capture
+  } else if (key == w.graph_seen && s->cfg.cuda_stream != nullptr) {
     // second call with the same buffers: capture the call as a graph, then replay it
     if (w.graph_exec) {
       cudaGraphExecDestroy(w.graph_exec);
@@ -1624,6 +1638,7 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
     w.graph_kernels = mpsk::thread_launches() - l0;
     mpsk::add_launches(-w.graph_kernels);   // captured, not launched: counted at each replay
     w.graph_key = key;
+    w.graph_ev_used = w.ev_used;
     MPS_CU(cudaGraphLaunch(w.graph_exec, s->st));
     add_launches(w.graph_kernels);
   } else {

@@ -379,3 +379,25 @@ def test_batched_device_outputs_and_instance_error(M):
     # the state recovers: the next call is clean
     E2, g2 = M.energy_grad(stb, circ, th, ham)
     assert np.array_equal(E2, E_h) and np.array_equal(g2, g_h)
+
+
+def test_profiling_events_survive_graph_replay(M):
+    """With profiling on, calls 2 (captured) and 3 (replayed) still time every SVD launch."""
+    import torch
+    p = S.make_problem(1)
+    excs = p.excitations[:6]
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    circ = M.Circuit(p.n, M.compile_excitations(p.n, excs))
+    ham = M.Hamiltonian(p.n, x, z, c)
+    th = np.stack([p.theta[: len(excs)]] * 2)
+    st = M.State.product_batch(np.stack([p.bits] * 2), p.spec.D, p.spec.eps, stream=torch.cuda.Stream())
+    st.profile(True)
+    res = []
+    for _ in range(3):
+        res.append(M.energy_grad(st, circ, th, ham))
+        pr = st.profile_read()
+        assert pr["svd_launches"] == circ.n_gates              # one event pair per SVD launch
+        assert pr["svd_launches_device"] == 2 * circ.n_gates   # one count per instance (CTA)
+        assert pr["svd_ms"] > 0.0
+    for E, g in res[1:]:
+        assert np.array_equal(E, res[0][0]) and np.array_equal(g, res[0][1])
