@@ -270,6 +270,14 @@ mps_status mps_svd_noalloc(int32_t m, int32_t ncol, const double* A, int32_t D, 
 mps_status mps_profile(mps_state* s, int32_t enable);
 mps_status mps_profile_read(mps_state* s, double* out6);
 
+/*
+ * Where the gate SVD's device time went, gathered by the mps_profile_read calls since the last
+ * call of this one (then reset): out6 = {ms in FP32 sweeps, ms re-orthonormalising Q and
+ * re-forming X = X0 Q in FP64, ms in FP64 sweeps, ms writing the outputs, FP32 sweeps run, FP64
+ * sweeps run}, each summed over launches and CTAs.  No counterpart in the paper.
+ */
+mps_status mps_profile_svd_phases(mps_state* s, double* out6);
+
 /* Release a state (NULL-safe). */
 void mps_free(mps_state* s);
 

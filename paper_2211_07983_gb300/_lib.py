@@ -77,6 +77,7 @@ _SIGS = {
                               c_void_p]),
     "mps_profile": (c_int32, [c_void_p, c_int32]),
     "mps_profile_read": (c_int32, [c_void_p, c_void_p]),
+    "mps_profile_svd_phases": (c_int32, [c_void_p, c_void_p]),
     "mps_free": (None, [c_void_p]),
     "mps_last_error": (ctypes.c_char_p, []),
     "mps_kernel_launches": (c_int64, []),

@@ -160,6 +160,13 @@ class State:
         return {"svd_ms": float(out[0]), "svd_launches": int(out[1]), "fp64_flops": float(out[2]),
                 "fp32_flops": float(out[3]), "svd_ms_device": float(out[4]), "svd_launches_device": int(out[5])}
 
+    def profile_phases(self) -> dict:
+        """mps_profile_svd_phases: SVD time per phase (ms) and sweeps, gathered by profile_read."""
+        out = np.zeros(6)
+        check(_lib.load().mps_profile_svd_phases(self._h, _ptr(out)))
+        return {"fp32_sweeps_ms": float(out[0]), "reform_ms": float(out[1]), "fp64_sweeps_ms": float(out[2]),
+                "output_ms": float(out[3]), "fp32_sweeps": float(out[4]), "fp64_sweeps": float(out[5])}
+
     def free(self):
         if self._h is not None and self._h.value:
             _lib.load().mps_free(self._h)

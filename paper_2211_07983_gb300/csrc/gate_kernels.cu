@@ -155,13 +155,27 @@ struct Cplx<float> {
 // rotations accumulated into Q (K x K, column j at Q + j*K).  One warp per column pair.  Column
 // norms are recomputed at the start of every sweep and updated by each rotation
 // (alpha' = alpha - t g, beta' = beta + t g), so a pair costs one inner product.
-// Returns the number of sweeps run; *converged = 1 if the last sweep rotated nothing.
+//
+// A pair (p, q) with inner product gamma is rotated when |gamma|^2 > tol^2 alpha beta.  The
+// rotation's tangent t = sign(zeta)/(|zeta| + sqrt(1 + zeta^2)), zeta = (beta - alpha)/(2|gamma|),
+// is computed in FP32; c = 1/sqrt(1 + t^2), s = c t and the phase gamma/|gamma| are then formed
+// in the working precision T, so every rotation is unitary to T's precision whatever the
+// accuracy of t (a t off by 1e-7 relative leaves |gamma| 1e-7 of its size, removed by the next
+// sweep at no extra sweep count, since the sweeps converge quadratically).  FP64 on GB300 runs at
+// 1/58 of the FP32 rate, and this keeps the divisions and square roots of a rotation in FP32.
+//
+// Stopping: a sweep that rotates nothing.  When `early` > 0, also a sweep whose largest rotated
+// |gamma|^2/(alpha beta) was <= early: the inner products that sweep leaves behind are then of
+// order K times that squared size, below tol, so the confirming sweep would rotate nothing.
+// Returns the number of sweeps run; *converged = 1 when a stopping rule was met.
 template <class T>
 __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int R, int K, T tol, T tiny,
-                             int max_sweeps, int* flag_sh, int* converged, T* nrm, double* flops) {
+                             int max_sweeps, int* flag_sh, int* converged, T* nrm, double* flops,
+                             double early, unsigned long long* maxrel_sh) {
   using C2 = typename Cplx<T>::t;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   const int Kp = K + (K & 1);
+  const T tol2 = tol * tol;
   int sweep = 0;
   long long checks = 0, rots = 0;   // per warp (lane 0's count is used)
   *converged = 0;
@@ -175,8 +189,12 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
       v = Cplx<T>::sum(v);
       if (lane == 0) nrm[j] = v;
     }
-    if (tid == 0) *flag_sh = 0;
+    if (tid == 0) {
+      *flag_sh = 0;
+      *maxrel_sh = 0ull;
+    }
     __syncthreads();
+    double maxrel = 0.0;   // this warp's largest rotated |gamma|^2/(alpha beta) in this sweep
     for (int r = 0; r < Kp - 1; ++r) {
       for (int t = warp; t < Kp / 2; t += nwarp) {
         int pc, qc;
@@ -201,12 +219,18 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
         }
         gr = Cplx<T>::sum(gr);
         gi = Cplx<T>::sum(gi);
-        const T g = hypot(gr, gi);
-        if (!(g > tol * sqrt(al) * sqrt(be))) continue;
-        const T zeta = (be - al) / (T(2) * g);
-        const T tt = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-        const T c = T(1) / sqrt(T(1) + tt * tt), s = c * tt;
-        const T pr = gr / g, pim = gi / g;                        // e^{i phi}
+        const T g2 = gr * gr + gi * gi;
+        const T ab = al * be;
+        if (!(g2 > tol2 * ab)) continue;
+        const T inv_g = rsqrt(g2);
+        const T g = g2 * inv_g;
+        const float zf = (float)((be - al) * (T(0.5) * inv_g));
+        const float af = fabsf(zf);
+        const float tf = af > 1e15f ? 0.5f / zf : copysignf(1.f / (af + sqrtf(1.f + zf * zf)), zf);
+        const T tt = (T)tf;
+        const T c = rsqrt(T(1) + tt * tt), s = c * tt;
+        const T pr = gr * inv_g, pim = gi * inv_g;                 // e^{i phi}
+        maxrel = fmax(maxrel, (double)(g2 / ab));
         // a_p' = c a_p - s e^{-i phi} a_q ; a_q' = s e^{i phi} a_p + c a_q
         const T spr = s * pr, spi = s * pim;
         for (int i = lane; i < R; i += 32) {
@@ -230,9 +254,13 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
       }
       __syncthreads();
     }
-    const int rot = *flag_sh;
+    // largest rotation of the sweep (non-negative doubles order like their bit patterns)
+    if (lane == 0 && maxrel > 0.0) atomicMax(maxrel_sh, (unsigned long long)__double_as_longlong(maxrel));
     __syncthreads();
-    if (!rot) {
+    const int rot = *flag_sh;
+    const double mr = __longlong_as_double((long long)*maxrel_sh);
+    __syncthreads();
+    if (!rot || (early > 0.0 && mr <= early)) {
       *converged = 1;
       ++sweep;
       break;
@@ -276,6 +304,7 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(const SvdArgs p0, size
   __shared__ double red[SVD_THREADS / 32];
   __shared__ double s_sh[512];
   __shared__ int flag_sh, conv_sh, k_sh;
+  __shared__ unsigned long long maxrel_sh;
   __shared__ double fro2_sh, smax_sh, nk_sh;
   const int b = p.b;
   const int Dl = p.dims[b], Dr = p.dims[b + 2];
@@ -311,8 +340,11 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(const SvdArgs p0, size
   }
   __syncthreads();
   int conv = 0;
-  jacobi_sweeps<float>(X32, Q32, R, K, 4.f * 1.1920929e-7f * sqrtf((float)R), (float)(1e-30 * fro2_sh) + 1e-37f,
-                       30, &flag_sh, &conv, reinterpret_cast<float*>(s_sh), p.stats ? p.stats + 1 : nullptr);
+  const int sweeps32 =
+      jacobi_sweeps<float>(X32, Q32, R, K, 4.f * 1.1920929e-7f * sqrtf((float)R), (float)(1e-30 * fro2_sh) + 1e-37f,
+                           30, &flag_sh, &conv, reinterpret_cast<float*>(s_sh), p.stats ? p.stats + 1 : nullptr,
+                           0.0, &maxrel_sh);
+  const unsigned long long t_fp32 = global_ns();
   // ---- Q64 = orthonormalised Q32 (modified Gram-Schmidt, FP64) ----
   for (int e = tid; e < K * K; e += SVD_THREADS) Q64[e] = make_double2((double)Q32[e].x, (double)Q32[e].y);
   __syncthreads();
@@ -350,8 +382,11 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(const SvdArgs p0, size
   }
   __syncthreads();
   // ---- FP64 sweeps ----
-  jacobi_sweeps<double>(X64, Q64, R, K, 4.0 * 2.220446049250313e-16 * sqrt((double)R), 1e-30 * fro2_sh,
-                        SVD_MAX_SWEEPS, &flag_sh, &conv_sh, s_sh, p.stats);
+  const unsigned long long t_reform = global_ns();
+  const double tol64 = 4.0 * 2.220446049250313e-16 * sqrt((double)R);
+  const int sweeps64 = jacobi_sweeps<double>(X64, Q64, R, K, tol64, 1e-30 * fro2_sh, SVD_MAX_SWEEPS, &flag_sh,
+                                             &conv_sh, s_sh, p.stats, tol64 / (2.0 * K), &maxrel_sh);
+  const unsigned long long t_fp64 = global_ns();
   // FP64 work outside the sweeps: Gram-Schmidt (~8 K^3) and X = X0 Q (8 R K^2)
   if (p.stats && tid == 0) atomicAdd(p.stats, 8.0 * K * K * (double)K + 8.0 * R * K * (double)K);
   if (tid == 0 && !conv_sh) set_status(p.status, MPS_ENOCONV);
@@ -432,9 +467,16 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(const SvdArgs p0, size
       p.tape_dims[4] = K;
     }
     p.dims[b + 1] = k;
-    if (p.stats) {   // device-side duration of this launch
-      atomicAdd(p.stats + 2, (double)(global_ns() - t_start));
+    if (p.stats) {   // device-side duration of this launch and of its phases
+      const unsigned long long t_end = global_ns();
+      atomicAdd(p.stats + 2, (double)(t_end - t_start));
       atomicAdd(p.stats + 3, 1.0);
+      atomicAdd(p.stats + 4, (double)(t_fp32 - t_start));
+      atomicAdd(p.stats + 5, (double)(t_reform - t_fp32));
+      atomicAdd(p.stats + 6, (double)(t_fp64 - t_reform));
+      atomicAdd(p.stats + 7, (double)(t_end - t_fp64));
+      atomicAdd(p.stats + 8, (double)sweeps32);
+      atomicAdd(p.stats + 9, (double)sweeps64);
     }
   }
 }

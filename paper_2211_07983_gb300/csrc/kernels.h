@@ -71,7 +71,9 @@ struct SvdArgs {
   const double* lam_left;
   double* lam_left_copy;
   int* status;
-  double* stats;   // optional: [0] += FP64 flops, [1] += FP32 flops, [2] += kernel ns, [3] += 1
+  double* stats;   // optional, 10 doubles: [0] += FP64 flops, [1] += FP32 flops, [2] += kernel ns, [3] += 1,
+                   // [4..7] += ns in FP32 sweeps / re-orthonormalisation and X0 Q / FP64 sweeps / output,
+                   // [8], [9] += FP32 and FP64 sweeps run
 };
 size_t svd_smem_bytes(int m_cap, int n_cap);
 bool svd_fits_smem(int m_cap, int n_cap);

@@ -155,7 +155,8 @@ struct Workspace {
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  DevBuf stats;            // 4 doubles per instance: FP64 flops, FP32 flops, SVD ns, SVD launches
+  DevBuf stats;            // 10 doubles per instance (see SvdArgs::stats)
+  double phases[6] = {0, 0, 0, 0, 0, 0};   // phase ms and sweeps, gathered by mps_profile_read
   double svd_ms = 0.0;
   long long svd_launches = 0;
   // captured energy+gradient call (see mps_energy_grad_dev)
@@ -1096,7 +1097,7 @@ mps_status mps_profile(mps_state* s, int32_t enable) {
   clear_error();
   if (!s) return fail(MPS_EINVAL, "mps_profile: state is NULL");
   Workspace& w = *s->ws;
-  MPS_TRY(w.stats.ensure(4 * sizeof(double)));
+  MPS_TRY(w.stats.ensure(10 * sizeof(double)));
   w.profile = enable != 0;
   return MPS_OK;
 }
@@ -1110,10 +1111,11 @@ mps_status mps_profile_read(mps_state* s, double* out6) {
     MPS_CU(cudaStreamSynchronize(s->st));
     for (int i = 0; i < s->n_inst(); ++i) {
       double* di = ish(w.stats.as<double>(), (size_t)i * s->arena->stride);
-      double fi[4];
+      double fi[10];
       MPS_CU(cudaMemcpy(fi, di, sizeof(fi), cudaMemcpyDeviceToHost));
       MPS_CU(cudaMemset(di, 0, sizeof(fi)));
       for (int q = 0; q < 4; ++q) fl[q] += fi[q];
+      for (int q = 0; q < 6; ++q) w.phases[q] += q < 4 ? fi[4 + q] * 1e-6 : fi[4 + q];
     }
   }
   out6[0] = w.svd_ms;
@@ -1124,6 +1126,17 @@ mps_status mps_profile_read(mps_state* s, double* out6) {
   out6[5] = fl[3];
   w.svd_ms = 0.0;
   w.svd_launches = 0;
+  return MPS_OK;
+}
+
+mps_status mps_profile_svd_phases(mps_state* s, double* out6) {
+  clear_error();
+  if (!s || !out6) return fail(MPS_EINVAL, "mps_profile_svd_phases: NULL argument");
+  Workspace& w = *s->ws;
+  for (int q = 0; q < 6; ++q) {
+    out6[q] = w.phases[q];
+    w.phases[q] = 0.0;
+  }
   return MPS_OK;
 }
 
@@ -1463,7 +1476,7 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
   MPS_TRY(stage_theta(s, theta, n_theta, &d_theta));
   MPS_TRY(ensure_forward_scratch(L, w));
   MPS_TRY(ensure_gate_matrices(s, c));
-  MPS_TRY(w.stats.ensure(4 * sizeof(double)));
+  MPS_TRY(w.stats.ensure(10 * sizeof(double)));
   w.ev_used = 0;
   const int ng = c->n_gates;
   // tape slot of one gate: pre-gate tensors, C, W, V, s, lambda_left, dims
