@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     return ap.parse_args()
 
 
@@ -260,6 +261,38 @@ def run_ours(args, rank, world, local):
     t_energy = (time.perf_counter() - t0) / n_rep
     terms_per_s = len(x) * B / t_energy
     st_f.free()
+    # ---- the mixed-precision path on the same instances (3xTF32 contractions and sweeps) ----
+    mixed = None
+    if not args.no_mixed:
+        E64, g64 = E_d.cpu().numpy().copy(), g_d.cpu().numpy().copy()
+        state.free()
+        torch.cuda.synchronize()
+        st_m = M.State.product_batch(np.stack([p.bits] * B), p.spec.D, p.spec.eps, checkpoint_every=0,
+                                     stream=stream, precision="mixed")
+        for _ in range(2):                      # eager, then captured
+            M.energy_grad(st_m, circ, thetas_d, ham, out=(E_d, g_d))
+        torch.cuda.synchronize()
+        ms_m = 0.0
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            M.energy_grad(st_m, circ, thetas_d, ham, out=(E_d, g_d))
+            e1.record(stream)
+            e1.synchronize()
+            ms_m += e0.elapsed_time(e1)
+        Em, gm = E_d.cpu().numpy(), g_d.cpu().numpy()
+        t_m = ms_m / 1e3 / args.steps
+        mixed = {"value": B * world / t_m, "unit": "evals/s", "ms_per_step": 1e3 * t_m,
+                 "speedup_vs_fp64": t_step / t_m,
+                 "max_rel_E_err_vs_fp64": float(np.max(np.abs(Em - E64) / np.maximum(1.0, np.abs(E64)))),
+                 "max_rel_grad_err_vs_fp64": float(np.max(np.linalg.norm(gm - g64, axis=1) /
+                                                          np.maximum(1.0, np.linalg.norm(g64, axis=1)))),
+                 "precision": "bond contractions and Pauli sweeps 3xTF32 on tensor cores (mma.sync, FP32 "
+                              "accumulation); SVD, SVD adjoint, sums FP64"}
+        st_m.free()
     # ---- roofline of the dominant kernel (the gate SVD: one CTA per instance per launch) ----
     roof = None
     n_launch = prof["svd_launches"]
@@ -290,6 +323,7 @@ def run_ours(args, rank, world, local):
                                                          "per-instance tape ~0.9 GB > L2",
                            "precision": "FP64 contractions; SVD FP32-preconditioned, FP64-finished"},
                 "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+                "mixed_precision": mixed,
                 "pauli_terms_per_s": {"value": terms_per_s, "unit": "Pauli-term expectations/s",
                                       "note": f"energy pass alone on the {B} final states "
                                               f"({len(x)} strings each), host clock over {n_rep} calls"}}

@@ -21,6 +21,7 @@ P = ctypes.POINTER
 STATUS = {0: "MPS_OK", 1: "MPS_EINVAL", 2: "MPS_ENOMEM", 3: "MPS_ECUDA", 4: "MPS_ENOCONV", 5: "MPS_ENUMERIC",
           6: "MPS_ETIMEOUT"}
 PRECISION_FP64 = 0
+PRECISION_MIXED = 1
 
 
 class MpsError(RuntimeError):

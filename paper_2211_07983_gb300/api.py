@@ -38,6 +38,12 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _precision(name: str) -> int:
+    if name not in ("fp64", "mixed"):
+        raise ValueError('precision must be "fp64" or "mixed"')
+    return _lib.PRECISION_FP64 if name == "fp64" else _lib.PRECISION_MIXED
+
+
 def _stream_handle(stream):
     if stream is None:
         return None
@@ -100,21 +106,25 @@ class State:
         self.n_inst = n_inst
 
     @classmethod
-    def product(cls, bits, max_bond: int, cutoff: float, checkpoint_every: int = 0, stream=None):
+    def product(cls, bits, max_bond: int, cutoff: float, checkpoint_every: int = 0, stream=None,
+                precision: str = "fp64"):
+        """precision: "fp64", or "mixed" (bond contractions and Pauli sweeps in 3xTF32 on the
+        tensor cores; SVD, SVD adjoint and sums in FP64)."""
         lib = _lib.load()
         bits = np.ascontiguousarray(bits, dtype=np.uint8)
-        cfg = MpsConfig(max_bond, cutoff, _lib.PRECISION_FP64, checkpoint_every, _stream_handle(stream))
+        cfg = MpsConfig(max_bond, cutoff, _precision(precision), checkpoint_every, _stream_handle(stream))
         h = ctypes.c_void_p()
         check(lib.mps_init_product(len(bits), bits.ctypes.data_as(P(ctypes.c_uint8)), ctypes.byref(cfg),
                                    ctypes.byref(h)))
         return cls(h, len(bits))
 
     @classmethod
-    def product_batch(cls, bits_rows, max_bond: int, cutoff: float, checkpoint_every: int = 0, stream=None):
+    def product_batch(cls, bits_rows, max_bond: int, cutoff: float, checkpoint_every: int = 0, stream=None,
+                      precision: str = "fp64"):
         """mps_init_product_batch: one product state per row of `bits_rows` ([n_inst, n])."""
         lib = _lib.load()
         bits = np.ascontiguousarray(np.atleast_2d(bits_rows), dtype=np.uint8)
-        cfg = MpsConfig(max_bond, cutoff, _lib.PRECISION_FP64, checkpoint_every, _stream_handle(stream))
+        cfg = MpsConfig(max_bond, cutoff, _precision(precision), checkpoint_every, _stream_handle(stream))
         h = ctypes.c_void_p()
         check(lib.mps_init_product_batch(bits.shape[0], bits.shape[1], bits.ctypes.data_as(P(ctypes.c_uint8)),
                                          ctypes.byref(cfg), ctypes.byref(h)))

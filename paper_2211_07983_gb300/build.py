@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmps.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-CU_SOURCES = ["mps_api.cu", "gemm.cu", "gate_kernels.cu", "energy_kernels.cu", "noalloc.cu", "arena.cu"]
+CU_SOURCES = ["mps_api.cu", "gemm.cu", "gate_kernels.cu", "energy_kernels.cu", "noalloc.cu", "arena.cu", "gemm_tf32.cu"]
 CXX_SOURCES = ["host_builders.cpp"]
 
 

@@ -27,6 +27,11 @@ struct GemmBatch {
   int count;
 };
 void launch_zgemm_small(const Batch& bt, const GemmBatch& b, int max_m, int max_n, cudaStream_t st);
+// The same two GEMMs on the tensor cores in split-TF32 (3xTF32) arithmetic, FP32 accumulation
+// (mixed-precision path; gemm_tf32.cu).
+void launch_zgemm_tf32x3_small(const Batch& bt, const GemmBatch& b, int max_m, int max_n, cudaStream_t st);
+void launch_zgemm_tf32x3_batched(const Batch& bt, const GemmDesc* d_descs, int count, int max_m, int max_n,
+                                 cudaStream_t st);
 
 // G (16 complex per gate) and dG/dphi from the gate table and theta (device).
 void launch_gate_matrices(const Batch& bt, const void* d_gates, int n_gates, const double* d_theta, int n_theta,

@@ -243,6 +243,16 @@ static mps_status record_profile_event(cudaEvent_t e, cudaStream_t st) {
 }
 
 // one gate on bond b: contract -> SVD/truncate -> update (Sec. 3); with a tape when `tp`
+// A per-gate GEMM.  Bond contractions (contraction = true) run on the tensor cores in 3xTF32 on
+// the mixed-precision path; the GEMMs of the SVD adjoint, whose 1/(s_i^2 - s_j^2) factors need
+// it, always run in FP64.
+static void gemm_small(const Ctx& cx, const GemmBatch& g, int max_m, int max_n, bool contraction) {
+  if (contraction && cx.cfg->precision == MPS_PRECISION_MIXED)
+    launch_zgemm_tf32x3_small(cx.bt, g, max_m, max_n, cx.st);
+  else
+    launch_zgemm_small(cx.bt, g, max_m, max_n, cx.st);
+}
+
 static mps_status forward_gate(Ctx& cx, StateBuf& sb, int b, const double2* Gt, const TapeSlot* tp) {
   const Layout& L = *cx.L;
   Workspace& w = *cx.ws;
@@ -288,7 +298,7 @@ static mps_status forward_gate(Ctx& cx, StateBuf& sb, int b, const double2* Gt, 
   g.count = 1;
   g.d[0] = make_desc(sb.dims, C, OP_N, Vs, OP_T, Bl, dref(b, 2), dref(b + 1), dref(b + 2, 2), dref(b + 2, 2),
                      dref(b + 2, 2), dref(b + 1));
-  launch_zgemm_small(cx.bt, g, 2 * L.cap[b], L.cap[b + 1], cx.st);
+  gemm_small(cx, g, 2 * L.cap[b], L.cap[b + 1], true);
   launch_vh_rows(cx.bt, Vs, sb.dims, b, Br, L.cap[b + 1], 2 * L.cap[b + 2], cx.st);
   return MPS_OK;
 }
@@ -320,21 +330,21 @@ static mps_status reverse_gate(Ctx& cx, int t, int b, const TapeSlot& tp, double
   g.d[0] = make_desc(td, tp.C, OP_H, Bbl, OP_N, w.Vbar, nc, k, m, nc, k, k, true);     // Vbar += C^H Bbar_b
   g.d[1] = make_desc(td, Bbl, OP_N, tp.Vs, OP_C, w.Cbar, m, nc, k, k, nc, nc);         // Cbar = Bbar_b V_k^H
   g.d[2] = make_desc(td, tp.Bl, OP_N, tp.Br, OP_N, w.Theta, m, nc, Dm, Dm, nc, nc);    // Theta = B_b B_{b+1}
-  launch_zgemm_small(cx.bt, g, std::max(mcap, ncap), std::max(kcap, ncap), cx.st);
+  gemm_small(cx, g, std::max(mcap, ncap), std::max(kcap, ncap), true);
   launch_sbar(cx.bt, lambar + L.lam_off[b + 1], tp.s, td, w.wbar, cx.st);              // sbar -> wbar
   g.count = 1;
   g.d[0] = make_desc(td, tp.Vs, OP_C, w.Vbar, OP_N, w.Y, Ks, k, nc, nc, k, k);         // Y = V_e^H Vbar
-  launch_zgemm_small(cx.bt, g, Kcap, kcap, cx.st);
+  gemm_small(cx, g, Kcap, kcap, false);
   g.d[0] = make_desc(td, tp.Vs, OP_T, w.Y, OP_N, w.Vbar, nc, k, Ks, nc, k, k, true, -1.0);   // Z = Vbar - V_e Y
-  launch_zgemm_small(cx.bt, g, ncap, kcap, cx.st);
+  gemm_small(cx, g, ncap, kcap, false);
   launch_build_K(cx.bt, w.Y, tp.s, w.wbar, td, w.Km, Kcap, cx.st);                            // diag(wbar)+J+J^H
   launch_zscale(cx.bt, w.Vbar, tp.s, td, ncap, kcap, cx.st);                                  // Z diag(1/w_k)
   g.d[0] = make_desc(td, tp.W, OP_T, w.Km, OP_N, w.T1, m, Ks, Ks, m, Ks, Ks);          // T1 = W K
-  launch_zgemm_small(cx.bt, g, mcap, Kcap, cx.st);
+  gemm_small(cx, g, mcap, Kcap, false);
   g.d[0] = make_desc(td, w.T1, OP_N, tp.Vs, OP_C, w.Ctbar, m, nc, Ks, Ks, nc, nc);     // C~bar = T1 V_e^H
-  launch_zgemm_small(cx.bt, g, mcap, ncap, cx.st);
+  gemm_small(cx, g, mcap, ncap, false);
   g.d[0] = make_desc(td, tp.W, OP_T, w.Vbar, OP_H, w.Ctbar, m, nc, k, m, k, nc, true);  // += W_k (Z/w)^H
-  launch_zgemm_small(cx.bt, g, mcap, ncap, cx.st);
+  gemm_small(cx, g, mcap, ncap, false);
   launch_lam_scale(cx.bt, w.Cbar, w.Ctbar, tp.C, tp.lamL, td, b > 0 ? lambar + L.lam_off[b] : nullptr, L.cap[b],
                    cx.st);
   launch_gbar(cx.bt, w.Cbar, w.Theta, td, dG + 16 * (size_t)t, w.Gbar, gate_grad + t, cx.st);
@@ -342,7 +352,7 @@ static mps_status reverse_gate(Ctx& cx, int t, int b, const TapeSlot& tp, double
   g.count = 2;
   g.d[0] = make_desc(td, w.Thbar, OP_N, tp.Br, OP_H, Bbl, m, Dm, nc, nc, nc, Dm);      // Bbar_b = Thbar B_{b+1}^H
   g.d[1] = make_desc(td, tp.Bl, OP_H, w.Thbar, OP_N, Bbr, Dm, nc, m, Dm, nc, nc);      // Bbar_{b+1} = B_b^H Thbar
-  launch_zgemm_small(cx.bt, g, std::max(mcap, kcap), std::max(kcap, ncap), cx.st);
+  gemm_small(cx, g, std::max(mcap, kcap), std::max(kcap, ncap), true);
   return MPS_OK;
 }
 
@@ -745,8 +755,10 @@ static mps_status build_energy_cache(const Layout& L, const StateBuf& sb, mps_ha
 }
 
 // Energy (and, when d_Bbar != null, the cotangent dE/dB* written in the state's site layout).
+// mixed: the transfer-matrix GEMMs run in 3xTF32 on the tensor cores (the sums stay FP64).
 static mps_status energy_pass_impl(const Layout& L, const StateBuf& sb, cudaStream_t st, int* status,
-                                   mps_hamiltonian_dev* h, double* d_E, double* d_expect, double2* d_Bbar) {
+                                   mps_hamiltonian_dev* h, double* d_E, double* d_expect, double2* d_Bbar,
+                                   bool mixed) {
   const Batch bt = sb.mem.arena->batch();
   if (!h->cache || h->cache->key_arena != sb.mem.arena->uid || h->cache->key_B != sb.B ||
       h->cache->key_dims != sb.dims || (d_Bbar && h->cache->key_Bbar != d_Bbar)) {
@@ -759,7 +771,12 @@ static mps_status energy_pass_impl(const Layout& L, const StateBuf& sb, cudaStre
   auto run = [&](const std::vector<Step>& plan) -> mps_status {
     for (const Step& s : plan) {
       switch (s.kind) {
-        case Step::GEMM: launch_zgemm_batched(bt, ec.d_desc + s.off, s.count, s.max_m, s.max_n, st); break;
+        case Step::GEMM:
+          if (mixed)
+            launch_zgemm_tf32x3_batched(bt, ec.d_desc + s.off, s.count, s.max_m, s.max_n, st);
+          else
+            launch_zgemm_batched(bt, ec.d_desc + s.off, s.count, s.max_m, s.max_n, st);
+          break;
         case Step::AXPY:
           launch_axpy_lists(bt, ec.d_axpy + s.off, s.count, ec.d_src, ec.d_srccoef, sb.dims, s.max_m, st);
           break;
@@ -885,7 +902,8 @@ static mps_status validate_config(const mps_config* cfg) {
   if (cfg->max_bond < 1 || cfg->max_bond > 256)
     return fail(MPS_EINVAL, "max_bond must be in 1..256");
   if (!(cfg->cutoff >= 0.0) || !std::isfinite(cfg->cutoff)) return fail(MPS_EINVAL, "cutoff must be finite and >= 0");
-  if (cfg->precision != MPS_PRECISION_FP64) return fail(MPS_EINVAL, "precision: only MPS_PRECISION_FP64 is built");
+  if (cfg->precision != MPS_PRECISION_FP64 && cfg->precision != MPS_PRECISION_MIXED)
+    return fail(MPS_EINVAL, "precision must be MPS_PRECISION_FP64 or MPS_PRECISION_MIXED");
   if (cfg->checkpoint_every < 0) return fail(MPS_EINVAL, "checkpoint_every must be >= 0");
   return MPS_OK;
 }
@@ -1329,7 +1347,7 @@ mps_status mps_energy_dev(const mps_state* s, const mps_hamiltonian_dev* h, doub
   double* dE = w.scalars.as<double>();
   double* dX = expect_out ? dE + 2 : nullptr;
   MPS_TRY(energy_pass_impl(s->L, s->buf, s->st, ms->status.as<int>(), const_cast<mps_hamiltonian_dev*>(h), dE, dX,
-                           nullptr));
+                           nullptr, s->cfg.precision == MPS_PRECISION_MIXED));
   MPS_TRY(put_out(ms, E_out, dE, 1));
   MPS_TRY(put_out(ms, expect_out, dX, nt));
   return finish_call(ms, "mps_energy");
@@ -1348,7 +1366,7 @@ mps_status mps_energy_cotangent_dev(const mps_state* s, const mps_hamiltonian_de
   MPS_TRY(w.Bbar.ensure(L.site_elems() * sizeof(double2)));
   double* dE = w.scalars.as<double>();
   MPS_TRY(energy_pass_impl(L, s->buf, s->st, ms->status.as<int>(), const_cast<mps_hamiltonian_dev*>(h), dE, nullptr,
-                           w.Bbar.as<double2>()));
+                           w.Bbar.as<double2>(), s->cfg.precision == MPS_PRECISION_MIXED));
   MPS_TRY(put_out(ms, E_out, dE, 1));
   MPS_TRY(finish_call(ms, "mps_energy_cotangent"));
   // dE/dB* of instance 0
@@ -1589,7 +1607,8 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
       }
     }
     // energy and its cotangent
-    MPS_TRY(energy_pass_impl(L, w.work, s->st, s->status.as<int>(), h, dE, nullptr, w.Bbar.as<double2>()));
+    MPS_TRY(energy_pass_impl(L, w.work, s->st, s->status.as<int>(), h, dE, nullptr, w.Bbar.as<double2>(),
+                             s->cfg.precision == MPS_PRECISION_MIXED));
     launch_zero_f64(cx.bt, w.lambar.as<double>(), L.lam_elems(), s->st);
     launch_zero_f64(cx.bt, w.gate_grad.as<double>(), std::max(1, ng), s->st);
     // reverse, segment by segment (re-running a segment's forward from its snapshot with a tape)

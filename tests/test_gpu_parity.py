@@ -401,3 +401,48 @@ def test_profiling_events_survive_graph_replay(M):
         assert pr["svd_ms"] > 0.0
     for E, g in res[1:]:
         assert np.array_equal(E, res[0][0]) and np.array_equal(g, res[0][1])
+
+
+# ---- mixed precision: 3xTF32 bond contractions and Pauli sweeps, FP64 SVD and SVD adjoint --------
+MIXED_E_TOL, MIXED_G_TOL = 1e-6, 1e-5
+
+
+@pytest.mark.parametrize("case", ["cfg0", "cfg1_prefix", "n8_trunc"])
+def test_mixed_precision_energy_grad_within_its_tolerance(M, case):
+    if case == "cfg0":
+        p, excs, D, eps = S.make_problem(0), None, None, None
+    elif case == "n8_trunc":
+        p = small(D=4, eps=1e-10)
+        excs, D, eps = p.excitations[:12], 4, 1e-10
+    else:
+        p = S.make_problem(1)
+        excs, D, eps = p.excitations[:30], None, None
+    excs = p.excitations if excs is None else excs
+    D = p.spec.D if D is None else D
+    eps = p.spec.eps if eps is None else eps
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    circ = M.Circuit(p.n, M.compile_excitations(p.n, excs))
+    ham = M.Hamiltonian(p.n, x, z, c)
+    th = p.theta[: len(excs)]
+    st = M.State.product(p.bits, D, eps, precision="mixed")
+    E, g = M.energy_grad(st, circ, th, ham)
+    r, _, _ = oracle(p, excs, D, eps)
+    assert abs(E - r.E) <= MIXED_E_TOL * max(1.0, abs(r.E))
+    assert np.linalg.norm(g - r.grad) <= MIXED_G_TOL * max(1.0, np.linalg.norm(r.grad))
+    # and the mixed path really differs from the FP64 path (the tensor-core GEMMs ran)
+    st64 = M.State.product(p.bits, D, eps)
+    E64, _ = M.energy_grad(st64, circ, th, ham)
+    assert E != E64
+
+
+def test_mixed_precision_full_config1(M):
+    """n = 12, D = 64, 117 excitations: mixed path within 1e-6 in E and 1e-5 in |g|."""
+    p = S.make_problem(1)
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    circ = M.Circuit(p.n, M.compile_excitations(p.n, p.excitations))
+    ham = M.Hamiltonian(p.n, x, z, c)
+    st = M.State.product(p.bits, p.spec.D, p.spec.eps, precision="mixed")
+    E, g = M.energy_grad(st, circ, p.theta, ham)
+    r, _, _ = oracle(p)
+    assert abs(E - r.E) <= MIXED_E_TOL * max(1.0, abs(r.E))
+    assert np.linalg.norm(g - r.grad) <= MIXED_G_TOL * max(1.0, np.linalg.norm(r.grad))
