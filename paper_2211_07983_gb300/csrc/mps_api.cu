@@ -243,13 +243,15 @@ static mps_status record_profile_event(cudaEvent_t e, cudaStream_t st) {
 }
 
 // one gate on bond b: contract -> SVD/truncate -> update (Sec. 3); with a tape when `tp`
-// A per-gate GEMM.  The bond contractions of the reverse pass (contraction = true) run on the
-// tensor cores in 3xTF32 on the mixed-precision path.  Two kinds always run in FP64.  The GEMMs
-// of the SVD adjoint need it because of their 1/(s_i^2 - s_j^2) factors.  The forward site
-// update needs it because its FP32-level rounding accumulates over thousands of gates: it
-// measured 1.5e-6 relative in E after 1400 gates, while one FP32-accurate energy pass costs 3e-8.
-static void gemm_small(const Ctx& cx, const GemmBatch& g, int max_m, int max_n, bool contraction) {
-  if (contraction && cx.cfg->precision == MPS_PRECISION_MIXED)
+// A per-gate GEMM; `mixed_ok` GEMMs run on the tensor cores in 3xTF32 on the mixed-precision
+// path.  Only the recomputed Theta = B_b B_{b+1} is: it feeds dE/dphi of its own gate and nothing
+// upstream.  Every other gate GEMM stays FP64.  The forward site update's FP32-level rounding
+// accumulates over the circuit: 1.5e-6 relative in E after 1400 gates, where the tolerance is
+// 1e-6.  The cotangents of the reverse pass reach the SVD adjoints of all earlier gates, whose
+// 1/(s_i^2 - s_j^2) factors amplify rounding at nearly degenerate Schmidt values: 1.1e-4
+// relative in |dE/dtheta| with them in 3xTF32, where the tolerance is 1e-5.
+static void gemm_small(const Ctx& cx, const GemmBatch& g, int max_m, int max_n, bool mixed_ok) {
+  if (mixed_ok && cx.cfg->precision == MPS_PRECISION_MIXED)
     launch_zgemm_tf32x3_small(cx.bt, g, max_m, max_n, cx.st);
   else
     launch_zgemm_small(cx.bt, g, max_m, max_n, cx.st);
@@ -328,11 +330,13 @@ static mps_status reverse_gate(Ctx& cx, int t, int b, const TapeSlot& tp, double
   const int mcap = 2 * L.cap[b], ncap = 2 * L.cap[b + 2], kcap = L.cap[b + 1], Kcap = std::min(mcap, ncap);
   launch_conjT(cx.bt, Bbr, td, w.Vbar, kcap, ncap, cx.st);                          // Vbar = Bbar_{b+1}^H
   GemmBatch g{};
-  g.count = 3;
+  g.count = 2;
   g.d[0] = make_desc(td, tp.C, OP_H, Bbl, OP_N, w.Vbar, nc, k, m, nc, k, k, true);     // Vbar += C^H Bbar_b
   g.d[1] = make_desc(td, Bbl, OP_N, tp.Vs, OP_C, w.Cbar, m, nc, k, k, nc, nc);         // Cbar = Bbar_b V_k^H
-  g.d[2] = make_desc(td, tp.Bl, OP_N, tp.Br, OP_N, w.Theta, m, nc, Dm, Dm, nc, nc);    // Theta = B_b B_{b+1}
-  gemm_small(cx, g, std::max(mcap, ncap), std::max(kcap, ncap), true);
+  gemm_small(cx, g, std::max(mcap, ncap), std::max(kcap, ncap), false);
+  g.count = 1;
+  g.d[0] = make_desc(td, tp.Bl, OP_N, tp.Br, OP_N, w.Theta, m, nc, Dm, Dm, nc, nc);    // Theta = B_b B_{b+1}
+  gemm_small(cx, g, mcap, ncap, true);
   launch_sbar(cx.bt, lambar + L.lam_off[b + 1], tp.s, td, w.wbar, cx.st);              // sbar -> wbar
   g.count = 1;
   g.d[0] = make_desc(td, tp.Vs, OP_C, w.Vbar, OP_N, w.Y, Ks, k, nc, nc, k, k);         // Y = V_e^H Vbar
@@ -354,7 +358,7 @@ static mps_status reverse_gate(Ctx& cx, int t, int b, const TapeSlot& tp, double
   g.count = 2;
   g.d[0] = make_desc(td, w.Thbar, OP_N, tp.Br, OP_H, Bbl, m, Dm, nc, nc, nc, Dm);      // Bbar_b = Thbar B_{b+1}^H
   g.d[1] = make_desc(td, tp.Bl, OP_H, w.Thbar, OP_N, Bbr, Dm, nc, m, Dm, nc, nc);      // Bbar_{b+1} = B_b^H Thbar
-  gemm_small(cx, g, std::max(mcap, kcap), std::max(kcap, ncap), true);
+  gemm_small(cx, g, std::max(mcap, kcap), std::max(kcap, ncap), false);
   return MPS_OK;
 }
 
