@@ -290,8 +290,9 @@ def run_ours(args, rank, world, local):
                  "max_rel_E_err_vs_fp64": float(np.max(np.abs(Em - E64) / np.maximum(1.0, np.abs(E64)))),
                  "max_rel_grad_err_vs_fp64": float(np.max(np.linalg.norm(gm - g64, axis=1) /
                                                           np.maximum(1.0, np.linalg.norm(g64, axis=1)))),
-                 "precision": "bond contractions and Pauli sweeps 3xTF32 on tensor cores (mma.sync, FP32 "
-                              "accumulation); SVD, SVD adjoint, sums FP64"}
+                 "precision": "energy Pauli sweeps and recomputed two-site tensors in 3xTF32 on tensor cores "
+                              "(mma.sync, FP32 accumulation); gate contractions, energy cotangent, SVD, SVD "
+                              "adjoint, sums FP64"}
         st_m.free()
     # ---- roofline of the dominant kernel (the gate SVD: one CTA per instance per launch) ----
     roof = None

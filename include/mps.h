@@ -59,14 +59,14 @@ typedef struct {
   double cutoff;             /* eps: keep singular values with s_i/||s||_2 > eps (values
                                 at or below 1e-13 s_1 are numerical zeros, never kept) */
   int32_t precision;         /* MPS_PRECISION_FP64: every contraction in FP64.
-                                MPS_PRECISION_MIXED: the Pauli transfer sweeps (energy and its
-                                cotangent) and the reverse pass's recomputed two-site tensors
-                                run on the tensor cores in split-TF32 (3xTF32, FP32
-                                accumulation).  The other gate contractions stay FP64: in
-                                3xTF32 their rounding, amplified by the SVD adjoint at nearly
-                                degenerate Schmidt values, exceeded 1e-5 in |dE/dtheta|.  The
-                                SVD, truncation, SVD adjoint and term sums are FP64.  Tensors
-                                are stored in FP64 either way. */
+                                MPS_PRECISION_MIXED: the Pauli transfer sweeps of the energy
+                                and the reverse pass's recomputed two-site tensors run on the
+                                tensor cores in split-TF32 (3xTF32, FP32 accumulation).  All
+                                that reaches the reverse pass's cotangents stays FP64 (gate
+                                contractions, the energy cotangent): the SVD adjoint amplifies
+                                rounding at nearly degenerate Schmidt values, and in 3xTF32 those
+                                exceeded 1e-5 in |dE/dtheta|.  The SVD, truncation, SVD adjoint
+                                and term sums are FP64.  Tensors are stored in FP64 either way. */
   int32_t checkpoint_every;  /* reverse pass: MPS snapshot every k gates, the segment
                                 re-run with a tape; 0 = automatic: one tape for the whole
                                 circuit when it fits in 60% of free device memory, else 512 */

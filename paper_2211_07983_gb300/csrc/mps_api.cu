@@ -761,7 +761,10 @@ static mps_status build_energy_cache(const Layout& L, const StateBuf& sb, mps_ha
 }
 
 // Energy (and, when d_Bbar != null, the cotangent dE/dB* written in the state's site layout).
-// mixed: the transfer-matrix GEMMs run in 3xTF32 on the tensor cores (the sums stay FP64).
+// mixed: the transfer-matrix GEMMs of the energy itself run in 3xTF32 on the tensor cores (the
+// sums stay FP64).  The cotangent dE/dB* is always FP64: it seeds the reverse pass, whose SVD
+// adjoints amplify its rounding at nearly degenerate Schmidt values (3xTF32 seeds moved
+// |dE/dtheta| by up to 7.7x its norm on some random-angle config-1 instances).
 static mps_status energy_pass_impl(const Layout& L, const StateBuf& sb, cudaStream_t st, int* status,
                                    mps_hamiltonian_dev* h, double* d_E, double* d_expect, double2* d_Bbar,
                                    bool mixed) {
@@ -774,11 +777,11 @@ static mps_status energy_pass_impl(const Layout& L, const StateBuf& sb, cudaStre
   }
   EnergyCache& ec = *h->cache;
   const int nt = (int)h->x.size();
-  auto run = [&](const std::vector<Step>& plan) -> mps_status {
+  auto run = [&](const std::vector<Step>& plan, bool tf32) -> mps_status {
     for (const Step& s : plan) {
       switch (s.kind) {
         case Step::GEMM:
-          if (mixed)
+          if (tf32)
             launch_zgemm_tf32x3_batched(bt, ec.d_desc + s.off, s.count, s.max_m, s.max_n, st);
           else
             launch_zgemm_batched(bt, ec.d_desc + s.off, s.count, s.max_m, s.max_n, st);
@@ -804,8 +807,8 @@ static mps_status energy_pass_impl(const Layout& L, const StateBuf& sb, cudaStre
     MPS_CU(cudaGetLastError());
     return MPS_OK;
   };
-  MPS_TRY(run(ec.plan_e));
-  if (d_Bbar) MPS_TRY(run(ec.plan_seed));
+  MPS_TRY(run(ec.plan_e, mixed));
+  if (d_Bbar) MPS_TRY(run(ec.plan_seed, false));
   return MPS_OK;
 }
 

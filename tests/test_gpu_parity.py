@@ -446,3 +446,21 @@ def test_mixed_precision_full_config1(M):
     r, _, _ = oracle(p)
     assert abs(E - r.E) <= MIXED_E_TOL * max(1.0, abs(r.E))
     assert np.linalg.norm(g - r.grad) <= MIXED_G_TOL * max(1.0, np.linalg.norm(r.grad))
+
+
+def test_mixed_precision_gradient_matches_fp64_on_random_instances(M):
+    """Random angles on a batch: the mixed path's gradient stays within 1e-5 of the FP64 path's."""
+    p = S.make_problem(1)
+    excs = p.excitations[:30]
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    circ = M.Circuit(p.n, M.compile_excitations(p.n, excs))
+    ham = M.Hamiltonian(p.n, x, z, c)
+    rng = np.random.default_rng(2024)
+    n_inst = 8
+    th = rng.uniform(-np.pi, np.pi, (n_inst, len(excs)))
+    bits = np.stack([p.bits] * n_inst)
+    E64, g64 = M.energy_grad(M.State.product_batch(bits, p.spec.D, p.spec.eps), circ, th, ham)
+    Em, gm = M.energy_grad(M.State.product_batch(bits, p.spec.D, p.spec.eps, precision="mixed"), circ, th, ham)
+    assert np.all(np.abs(Em - E64) <= MIXED_E_TOL * np.maximum(1.0, np.abs(E64)))
+    rel = np.linalg.norm(gm - g64, axis=1) / np.maximum(1.0, np.linalg.norm(g64, axis=1))
+    assert rel.max() <= MIXED_G_TOL
