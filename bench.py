@@ -285,11 +285,15 @@ def run_ours(args, rank, world, local):
             ms_m += e0.elapsed_time(e1)
         Em, gm = E_d.cpu().numpy(), g_d.cpu().numpy()
         t_m = ms_m / 1e3 / args.steps
+        g_rel = np.linalg.norm(gm - g64, axis=1) / np.maximum(1.0, np.linalg.norm(g64, axis=1))
         mixed = {"value": B * world / t_m, "unit": "evals/s", "ms_per_step": 1e3 * t_m,
                  "speedup_vs_fp64": t_step / t_m,
                  "max_rel_E_err_vs_fp64": float(np.max(np.abs(Em - E64) / np.maximum(1.0, np.abs(E64)))),
-                 "max_rel_grad_err_vs_fp64": float(np.max(np.linalg.norm(gm - g64, axis=1) /
-                                                          np.maximum(1.0, np.linalg.norm(g64, axis=1)))),
+                 "rel_grad_err_vs_fp64": {"median": float(np.median(g_rel)),
+                                          "p90": float(np.percentile(g_rel, 90)), "max": float(g_rel.max()),
+                                          "fraction_within_1e-5": float(np.mean(g_rel <= 1e-5))},
+                 "grad_note": "instances whose exact adjoint meets nearly degenerate Schmidt values amplify any "
+                              "1e-7 change of E (here the mixed E) by the SVD adjoint's 1/(s_i^2 - s_j^2)",
                  "precision": "energy Pauli sweeps and recomputed two-site tensors in 3xTF32 on tensor cores "
                               "(mma.sync, FP32 accumulation); gate contractions, energy cotangent, SVD, SVD "
                               "adjoint, sums FP64"}
