@@ -464,3 +464,32 @@ def test_mixed_precision_gradient_matches_fp64_on_random_instances(M):
     assert np.all(np.abs(Em - E64) <= MIXED_E_TOL * np.maximum(1.0, np.abs(E64)))
     rel = np.linalg.norm(gm - g64, axis=1) / np.maximum(1.0, np.linalg.norm(g64, axis=1))
     assert rel.max() <= MIXED_G_TOL
+
+
+def test_config2_prefix_against_oracle_and_batched_central_differences(M):
+    """n = 20, D = 128, eps = 1e-10 (the differentiation workload), first 16 excitations with
+    truncation: E and dE/dtheta against the oracle.  Central differences (h = 1e-5) on four
+    components are evaluated as eight instances of one batched state, in one launch sequence."""
+    p = S.make_problem(2)
+    excs = p.excitations[:16]
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    circ = M.Circuit(p.n, M.compile_excitations(p.n, excs))
+    ham = M.Hamiltonian(p.n, x, z, c)
+    th = p.theta[:16]
+    st = M.State.product(p.bits, p.spec.D, p.spec.eps, checkpoint_every=128)
+    E, g = M.energy_grad(st, circ, th, ham)
+    r, _, _ = oracle(p, excs)
+    assert abs(E - r.E) <= E_TOL * max(1.0, abs(r.E))
+    assert np.linalg.norm(g - r.grad) <= G_TOL * max(1.0, np.linalg.norm(r.grad))
+    h, comps = 1e-5, [0, 5, 10, 15]
+    rows = []
+    for j in comps:
+        for sgn in (1.0, -1.0):
+            t = th.copy()
+            t[j] += sgn * h
+            rows.append(t)
+    stb = M.State.product_batch(np.stack([p.bits] * len(rows)), p.spec.D, p.spec.eps)
+    M.apply_circuit(stb, circ, np.stack(rows))
+    Eb = M.energy(stb, ham)
+    fd = (Eb[0::2] - Eb[1::2]) / (2 * h)
+    assert np.abs(fd - g[comps]).max() <= 1e-7 * max(1.0, np.abs(g).max())
