@@ -568,16 +568,24 @@ __global__ void build_K_kernel(const double2* __restrict__ Y, const double* __re
   Km[(size_t)i * K + j] = v;
 }
 
-// Z[r][j] /= w_j (j < k): the complement term (W_k diag(1/w_k)) Z^H of the SVD adjoint
+// Z[r][j] /= w_j (j < k): the complement term (W_k diag(1/w_k)) Z^H of the SVD adjoint.  When
+// the SVD's K vectors span the whole column space (K = ncol), the complement is empty and Z =
+// Vbar - V V^H Vbar is zero.  Computed, it is rounding of size 1e-16 |Vbar|, and 1/w_k of a kept
+// value just above the cutoff (w ~ 1e-24 w_1) turns that into a gradient error of many times
+// the gradient's norm.  The term is therefore set to exactly zero.
 __global__ void zscale_kernel(double2* Z, const double* __restrict__ s, const int* __restrict__ td,
                               size_t stride) {
   const size_t io = (size_t)blockIdx.y * stride;
   Z = ish(Z, io);
   s = ish(s, io);
   td = ish(td, io);
-  const int k = td[3], n = 2 * td[2];
+  const int k = td[3], n = 2 * td[2], K = td[4];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * k) return;
+  if (K >= n) {
+    Z[t] = make_double2(0.0, 0.0);
+    return;
+  }
   const int j = t % k;
   Z[t] = cscale(Z[t], 1.0 / (s[j] * s[j]));
 }
