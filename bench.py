@@ -313,8 +313,8 @@ def run_ours(args, rank, world, local):
                  "rel_grad_err_vs_fp64": {"median": float(np.median(g_rel)),
                                           "p90": float(np.percentile(g_rel, 90)), "max": float(g_rel.max()),
                                           "fraction_within_1e-5": float(np.mean(g_rel <= 1e-5))},
-                 "grad_note": "the large differences come from instances that keep Schmidt values just above "
-                              "eps, where the FP64 GPU gradient itself departs from the exact one",
+                 "grad_note": "large differences come from rare ill-conditioned instances that keep Schmidt "
+                              "values just above eps",
                  "precision": "energy Pauli sweeps and recomputed two-site tensors in 3xTF32 on tensor cores "
                               "(mma.sync, FP32 accumulation); gate contractions, energy cotangent, SVD, SVD "
                               "adjoint, sums FP64"}
