@@ -493,3 +493,24 @@ def test_config2_prefix_against_oracle_and_batched_central_differences(M):
     Eb = M.energy(stb, ham)
     fd = (Eb[0::2] - Eb[1::2]) / (2 * h)
     assert np.abs(fd - g[comps]).max() <= 1e-7 * max(1.0, np.abs(g).max())
+
+
+def test_gradient_with_kept_schmidt_values_just_above_the_cutoff(M):
+    """Config 1 at two random angle sets that keep Schmidt values of 2-4e-12 s_1 (instances 29 and
+    144 of a seeded batch).  Nothing is truncated, so the dense state-vector gradient is exact.
+    These spectra exposed rounding in the SVD adjoint's complement term (1/w_k of a tiny kept
+    value), which is zero whenever the singular vectors span the column space."""
+    p = S.make_problem(1)
+    n_theta = len(p.excitations)
+    th = np.stack([S.random_theta(S.seed_for(1, 500 + i), n_theta) for i in (29, 144)])
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    circ = M.Circuit(p.n, M.compile_excitations(p.n, p.excitations))
+    ham = M.Hamiltonian(p.n, x, z, c)
+    st = M.State.product_batch(np.stack([p.bits] * 2), p.spec.D, p.spec.eps)
+    E, g = M.energy_grad(st, circ, th, ham)
+    og = ansatz.compile_circuit(p.n, p.excitations)
+    oh = pauli.jw_hamiltonian(p.h, p.eri)
+    for r in range(2):
+        Es, gs, _ = SV.gradient(p.bits, og, th[r], oh)
+        assert abs(E[r] - Es) < 1e-10 * abs(Es)
+        assert np.linalg.norm(g[r] - gs) <= 1e-7 * np.linalg.norm(gs)
