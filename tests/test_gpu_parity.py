@@ -514,3 +514,28 @@ def test_gradient_with_kept_schmidt_values_just_above_the_cutoff(M):
         Es, gs, _ = SV.gradient(p.bits, og, th[r], oh)
         assert abs(E[r] - Es) < 1e-10 * abs(Es)
         assert np.linalg.norm(g[r] - gs) <= 1e-7 * np.linalg.norm(gs)
+
+
+def test_config2_prefix_parameter_shift_on_eight_gate_angles(M):
+    """Parameter shift (Sec. 4, Eq. psr) on 8 Rz gates of the n = 20, D = 128 prefix: each chosen
+    gate gets its own extra angle, and phi +- pi/2 are evaluated as the two instances of a batched
+    state.  Half their energy difference is dE/dphi of that gate, which the reverse pass returns."""
+    p = S.make_problem(2)
+    excs = p.excitations[:16]
+    gates = M.compile_excitations(p.n, excs)
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    ham = M.Hamiltonian(p.n, x, z, c)
+    th = p.theta[:16]
+    st = M.State.product(p.bits, p.spec.D, p.spec.eps)
+    _, _, gg = M.energy_grad(st, M.Circuit(p.n, gates), th, ham, gate_grad=True)
+    par = np.flatnonzero(gates["theta_idx"] >= 0)
+    picks = par[np.linspace(0, len(par) - 1, 8).astype(int)]
+    for t in picks:
+        g2 = gates.copy()
+        j, sc = int(g2["theta_idx"][t]), float(g2["theta_scale"][t])
+        g2["theta_idx"][t] = len(th)
+        rows = np.stack([np.concatenate([th, [th[j] + sgn * (np.pi / 2) / sc]]) for sgn in (1.0, -1.0)])
+        stb = M.State.product_batch(np.stack([p.bits] * 2), p.spec.D, p.spec.eps)
+        M.apply_circuit(stb, M.Circuit(p.n, g2), rows)
+        E = M.energy(stb, ham)
+        assert abs(0.5 * (E[0] - E[1]) - gg[t]) <= 1e-8 * max(1.0, np.abs(gg).max())
