@@ -88,7 +88,7 @@ def apply_gate(mps: MPS, bond: int, G: np.ndarray, D: int, eps: float, keep_tape
     n0 = bond
     Bl, Br = mps.B[n0], mps.B[n0 + 1]
     Dl, Dr = Bl.shape[0], Br.shape[2]
-    theta4 = np.einsum("aim,mjc->aijc", Bl, Br)
+    theta4 = two_site(Bl, Br)
     C = np.einsum("xy,ayc->axc", G, theta4.reshape(Dl, 4, Dr)).reshape(Dl, 2, 2, Dr)
     lam_left = mps.lam[n0 - 1] if n0 > 0 else np.ones(1)
     Ct = lam_left[:, None, None, None] * C
@@ -118,25 +118,39 @@ def apply_circuit(mps: MPS, gates, theta, D: int, eps: float, phi_override=None)
 
 # ---- contractions ----------------------------------------------------------------
 
+# The sums over bond indices below are written as matrix products of reshaped tensors (the
+# same contractions; a library matmul is one step), the 2x2 operator on the physical index as
+# an einsum.
+
+def two_site(Bl, Br):
+    """Theta[a, i, j, c] = sum_m Bl[a, i, m] Br[m, j, c]."""
+    Dl, _, Dm = Bl.shape
+    Dr = Br.shape[2]
+    return (Bl.reshape(2 * Dl, Dm) @ Br.reshape(Dm, 2 * Dr)).reshape(Dl, 2, 2, Dr)
+
+
 def transfer_left(L, B, O):
     """L'[b', b] = sum conj(B[a', i', b']) O[i', i] L[a', a] B[a, i, b]."""
-    T = np.einsum("xa,aib->xib", L, B)
-    T = np.einsum("ji,xib->xjb", O, T)
-    return np.einsum("xjy,xjb->yb", B.conj(), T)
+    Dl, _, Dr = B.shape
+    T = (L @ B.reshape(Dl, 2 * Dr)).reshape(L.shape[0], 2, Dr)      # sum_a L[a', a] B[a, i, b]
+    T = np.einsum("ji,xib->xjb", O, T)                               # O on the physical index
+    return B.reshape(2 * Dl, Dr).conj().T @ T.reshape(2 * Dl, Dr)    # sum_{a', i'} conj(B[a', i', b'])
 
 
 def transfer_right(R, B, O):
     """R'[a', a] = sum conj(B[a', i', b']) O[i', i] B[a, i, b] R[b', b]."""
-    T = np.einsum("aib,yb->aiy", B, R)
+    Dl, _, Dr = B.shape
+    T = (B.reshape(2 * Dl, Dr) @ R.T).reshape(Dl, 2, R.shape[0])     # sum_b B[a, i, b] R[b', b]
     T = np.einsum("ji,aiy->ajy", O, T)
-    return np.einsum("xjy,ajy->xa", B.conj(), T)
+    return B.reshape(Dl, 2 * Dr).conj() @ T.reshape(Dl, 2 * Dr).T   # sum_{i', b'} conj(B[a', i', b'])
 
 
 def site_env(L, O, B, R):
     """d<psi|O|psi>/d conj(B[a', i', b']) = sum L[a', a] O[i', i] B[a, i, b] R[b', b]."""
-    T = np.einsum("xa,aib->xib", L, B)
+    Dl, _, Dr = B.shape
+    T = (L @ B.reshape(Dl, 2 * Dr)).reshape(L.shape[0], 2, Dr)
     T = np.einsum("ji,xib->xjb", O, T)
-    return np.einsum("xjb,yb->xjy", T, R)
+    return (T.reshape(-1, Dr) @ R.T).reshape(L.shape[0], 2, R.shape[0])
 
 
 def identity_envs(mps: MPS):
@@ -270,13 +284,15 @@ def gate_adjoint(tape, Bbar_l_new, Bbar_r_new, lambar_new, dG):
     Ctbar = svd_adjoint(Cm, s, V, k, sbar_k, Vbar_k).reshape(Dl, 2, 2, Dr)
     Cbar = Cbar.reshape(Dl, 2, 2, Dr) + lam_left[:, None, None, None] * Ctbar
     lambar_left = 2.0 * np.real(np.einsum("aijc,aijc->a", Ctbar.conj(), C))
-    theta4 = np.einsum("aim,mjc->aijc", Bl, Br).reshape(Dl, 4, Dr)
+    theta4 = two_site(Bl, Br).reshape(Dl, 4, Dr)
     Cb4 = Cbar.reshape(Dl, 4, Dr)
     Gbar = np.einsum("axc,ayc->xy", Cb4, theta4.conj())
     dphi = 2.0 * float(np.real(np.sum(Gbar.conj() * dG)))
     Thbar = np.einsum("xy,axc->ayc", G.conj(), Cb4).reshape(Dl, 2, 2, Dr)
-    Bbar_l = np.einsum("aijc,mjc->aim", Thbar, Br.conj())
-    Bbar_r = np.einsum("aim,aijc->mjc", Bl.conj(), Thbar)
+    Dm = Bl.shape[2]
+    Th2 = Thbar.reshape(2 * Dl, 2 * Dr)
+    Bbar_l = (Th2 @ Br.reshape(Dm, 2 * Dr).conj().T).reshape(Dl, 2, Dm)   # sum_{j,c} Thbar conj(Br)
+    Bbar_r = (Bl.reshape(2 * Dl, Dm).conj().T @ Th2).reshape(Dm, 2, Dr)   # sum_{a,i} conj(Bl) Thbar
     return Bbar_l, Bbar_r, lambar_left, dphi
 
 
