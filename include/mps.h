@@ -223,6 +223,10 @@ mps_status mps_energy_cotangent_dev(const mps_state* s, const mps_hamiltonian_de
  * n_gates doubles receiving dE/dphi of each gate's Rz angle (0 for fixed gates).
  * All three outputs: host or device.
  */
+/* The host-argument calls mps_apply_circuit, mps_energy and mps_energy_grad upload their gate
+ * list and Hamiltonian into the state's workspace.  The last upload of each is kept with a copy of
+ * its contents and reused while later calls on the same state pass equal contents, so a repeated
+ * call reuses the sweep trie, the energy plan and the captured evaluation graph. */
 mps_status mps_energy_grad(const mps_state* s0, const mps_gate* gates, int32_t n_gates,
                            const double* theta, int32_t n_theta, const mps_hamiltonian* h,
                            double* E_out, double* grad_out, double* gate_grad_out);
@@ -245,20 +249,22 @@ mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, doub
                        double* V_out, double* W_out, int32_t* k_out);
 
 /*
- * The gate SVD of mps_svd_dev without any memory allocation, for callers that cannot allocate
- * device memory: code that runs while a CUDA graph is being captured (cudaMalloc cannot be
- * captured), code in latency-critical loops where the implicit device synchronisation of
- * cudaMalloc/cudaFree is not acceptable, and embedders whose device memory is owned by another
- * allocator.  The paper has no counterpart; this is a service of the library.
+ * The gate SVD of mps_svd_dev without any memory allocation.  Some callers cannot call
+ * cudaMalloc: embedders whose device memory is owned by another allocator (a framework's caching
+ * allocator, a memory pool sized once at start-up) or that run under a fixed device-memory budget,
+ * and latency-critical loops that cannot pay for the device-wide synchronisation that
+ * cudaMalloc/cudaFree can imply.  This entry point serves them from a fixed scratch array inside
+ * the library.  The paper has no counterpart; this is a service of the library.
  *   m, ncol: even, 2..128 (larger sizes are rejected with MPS_EINVAL: the scratch is fixed).
- *   A, s_out, V_out, W_out, k_out: device memory owned by the caller, same layouts and meaning
- *   as in mps_svd_dev (K = min(m, ncol)).  cuda_stream: cudaStream_t or NULL.
+ *   A, s_out, V_out, W_out, k_out: device memory of the current device, owned by the caller, same
+ *   layouts and meaning as in mps_svd_dev (K = min(m, ncol)); memory of another device is
+ *   rejected with MPS_EINVAL.  cuda_stream: cudaStream_t or NULL.
  * Scratch: one file-scope device array of about 1.25 MiB inside the library, held by every GPU
  * that loads the library until the process exits.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls on a device share the array, which keeps the last
- * call's contents: calls that overlap on the GPU (different streams or threads) race and must
- * be serialised by the caller.  The call synchronises `cuda_stream` to read the status word.
+ * array's device address (cudaGetSymbolAddress) with that device current.  All calls on a device
+ * share the array, which keeps the last call's contents (the call clears what must start at
+ * zero): calls that overlap on the GPU (different streams or threads) race and must be
+ * serialised by the caller.  The call synchronises `cuda_stream` to read the status word.
  */
 mps_status mps_svd_noalloc(int32_t m, int32_t ncol, const double* A, int32_t D, double eps, double* s_out,
                            double* V_out, double* W_out, int32_t* k_out, void* cuda_stream);

@@ -6,8 +6,10 @@ include/mps.h).  This package holds its ctypes binding (`api`), the autograd wra
 (`parallel`).  Importing the package does not load the library; the first call does,
 and fails loudly if the library was not built.
 """
-from .api import (Circuit, Hamiltonian, State, apply_circuit, build_hamiltonian, compile_excitations, energy,
-                  energy_cotangent, energy_grad, kernel_launches, svd)
+from .api import (Circuit, Hamiltonian, State, apply_circuit, apply_circuit_host, build_hamiltonian,
+                  compile_excitations, energy, energy_cotangent, energy_grad, energy_grad_host, energy_host,
+                  kernel_launches, svd)
 
-__all__ = ["Circuit", "Hamiltonian", "State", "apply_circuit", "build_hamiltonian", "compile_excitations",
-           "energy", "energy_cotangent", "energy_grad", "kernel_launches", "svd"]
+__all__ = ["Circuit", "Hamiltonian", "State", "apply_circuit", "apply_circuit_host", "build_hamiltonian",
+           "compile_excitations", "energy", "energy_cotangent", "energy_grad", "energy_grad_host", "energy_host",
+           "kernel_launches", "svd"]

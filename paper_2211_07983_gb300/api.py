@@ -302,6 +302,44 @@ def energy_grad(state0: State, circuit: Circuit, theta, ham: Hamiltonian, out=No
     return (E, g_out, gg) if gate_grad else (E, g_out)
 
 
+# ---- the host-argument calls of include/mps.h (gate list and Hamiltonian passed per call) -----
+
+def _gates_arg(gates):
+    gates = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    return gates, ctypes.c_void_p(gates.ctypes.data) if len(gates) else None
+
+
+def apply_circuit_host(state: State, gates, theta) -> None:
+    """mps_apply_circuit: gate list as a host array of mps_gate (GATE_DTYPE)."""
+    theta = _f64(theta)
+    gates, gp = _gates_arg(gates)
+    check(_lib.load().mps_apply_circuit(state._h, gp, len(gates), _ptr(theta), _n_theta(state, theta)))
+
+
+def energy_host(state: State, x, z, c):
+    """mps_energy: Hamiltonian as host arrays (x_mask, z_mask, coeff)."""
+    hs, _keep = _ham_struct(x, z, c)
+    E = np.zeros(state.n_inst)
+    check(_lib.load().mps_energy(state._h, ctypes.byref(hs), _ptr(E)))
+    return float(E[0]) if state.n_inst == 1 else E
+
+
+def energy_grad_host(state0: State, gates, theta, x, z, c, gate_grad=False):
+    """mps_energy_grad: gate list and Hamiltonian as host arrays."""
+    theta = _f64(theta)
+    nth = _n_theta(state0, theta)
+    gates, gp = _gates_arg(gates)
+    hs, _keep = _ham_struct(x, z, c)
+    ni = state0.n_inst
+    E = np.zeros(ni)
+    g = np.zeros((ni, nth) if ni > 1 else nth)
+    gg = (np.zeros((ni, len(gates)) if ni > 1 else len(gates))) if gate_grad else None
+    check(_lib.load().mps_energy_grad(state0._h, gp, len(gates), _ptr(theta), nth, ctypes.byref(hs), _ptr(E),
+                                      _ptr(g), _ptr(gg)))
+    Ev = float(E[0]) if ni == 1 else E
+    return (Ev, g, gg) if gate_grad else (Ev, g)
+
+
 def svd(A: np.ndarray, D: int, eps: float):
     """mps_svd_dev: the GPU gate SVD of one complex matrix -> (s, V, W = A V, k)."""
     A = np.ascontiguousarray(A, dtype=np.complex128)

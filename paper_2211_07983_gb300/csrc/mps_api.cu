@@ -119,15 +119,32 @@ mps_status StateBuf::copy_from(const StateBuf& o, const Layout& L, cudaStream_t 
   return MPS_OK;
 }
 
-static bool is_device_ptr(const void* p) {
-  if (!p) return false;
+PtrLocation ptr_location(const void* p) {
+  if (!p) return PTR_HOST;
   cudaPointerAttributes a{};
   cudaError_t e = cudaPointerGetAttributes(&a, p);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return PTR_HOST;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return PTR_DEVICE;
+  if (a.type != cudaMemoryTypeDevice) return PTR_HOST;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return PTR_OTHER_DEVICE;
+  }
+  return a.device == dev ? PTR_DEVICE : PTR_OTHER_DEVICE;
+}
+
+// A caller's array: host (false) or device memory of the current device (true).  Memory of
+// another device is rejected with MPS_EINVAL (the kernels run on the current device only).
+static mps_status where_is(const void* p, const char* what, bool* dev) {
+  const PtrLocation l = ptr_location(p);
+  if (l == PTR_OTHER_DEVICE)
+    return fail(MPS_EINVAL, std::string(what) + " points to memory of another device");
+  *dev = l == PTR_DEVICE;
+  return MPS_OK;
 }
 
 // ---- workspace ------------------------------------------------------------------------------
@@ -179,6 +196,15 @@ struct Workspace {
   cudaEvent_t done = nullptr;     // blocking-sync event: waiting threads sleep instead of spinning
   long long auto_uid = -1;        // circuit for which the automatic checkpoint interval was chosen
   int auto_K = 0;
+  // Host-argument calls (mps_apply_circuit, mps_energy, mps_energy_grad) upload their gate list
+  // and Hamiltonian; the last uploads are kept with a copy of their contents and reused while a
+  // caller passes the same contents, so that the energy plan and the captured graph of a
+  // repeated call are reused too.
+  std::unique_ptr<mps_circuit> host_circ;
+  std::vector<mps_gate> host_circ_gates;
+  std::unique_ptr<mps_hamiltonian_dev> host_ham;
+  std::vector<uint64_t> host_ham_x, host_ham_z;
+  std::vector<double> host_ham_c;
   explicit Workspace(Arena* a)
       : arena(a), A(a), svd(a), C(a), Vs(a), s(a), G(a), dG(a), theta(a), scalars(a), gate_grad(a), grad(a),
         work(a), rec(a), tape(a), Bbar(a), lambar(a), rv(a), stats(a) {}
@@ -974,7 +1000,9 @@ static mps_status stage_theta(mps_state* s, const double* theta, int n_theta, co
   *d_theta = w.theta.as<double>();
   if (n_theta == 0) return MPS_OK;
   const size_t row = (size_t)n_theta * sizeof(double);
-  if (is_device_ptr(theta)) {   // finiteness is checked by the gate-matrix kernel
+  bool theta_dev = false;
+  MPS_TRY(where_is(theta, "theta", &theta_dev));
+  if (theta_dev) {   // finiteness is checked by the gate-matrix kernel
     launch_copy_f64(bt, w.theta.as<double>(), bt.stride, theta, row, n_theta, s->st);
     return MPS_OK;
   }
@@ -994,7 +1022,9 @@ static mps_status put_out(mps_state* s, double* dst, const double* dsrc, size_t 
   Workspace& w = *s->ws;
   const Batch bt = s->batch();
   const size_t row = count * sizeof(double);
-  if (is_device_ptr(dst)) {
+  bool dst_dev = false;
+  MPS_TRY(where_is(dst, "an output array", &dst_dev));
+  if (dst_dev) {
     launch_copy_f64(bt, dst, row, dsrc, bt.stride, count, s->st);
     return MPS_OK;
   }
@@ -1020,6 +1050,47 @@ static void gate_matrices_launch(mps_state* s, const mps_circuit* c, const doubl
 static mps_status gate_matrices(mps_state* s, const mps_circuit* c, const double* d_theta, int n_theta) {
   MPS_TRY(ensure_gate_matrices(s, c));
   gate_matrices_launch(s, c, d_theta, n_theta);
+  return MPS_OK;
+}
+
+// The state's upload of a host gate list: reused when the contents equal the last upload's.
+static mps_status host_circuit(mps_state* s, const mps_gate* gates, int32_t n_gates, const mps_circuit** out) {
+  Workspace& w = *s->ws;
+  if (n_gates < 0 || (n_gates > 0 && !gates)) return fail(MPS_EINVAL, "bad gate array");
+  if (w.host_circ && (int)w.host_circ_gates.size() == n_gates &&
+      (n_gates == 0 || std::memcmp(w.host_circ_gates.data(), gates, (size_t)n_gates * sizeof(mps_gate)) == 0)) {
+    *out = w.host_circ.get();
+    return MPS_OK;
+  }
+  mps_circuit* c = nullptr;
+  MPS_TRY(mps_circuit_create(s->L.n, gates, n_gates, &c));
+  w.host_circ.reset(c);
+  w.host_circ_gates.assign(gates, gates + n_gates);
+  *out = c;
+  return MPS_OK;
+}
+
+// The state's upload of a host Hamiltonian: reused when the strings and coefficients equal the
+// last upload's.
+static mps_status host_hamiltonian(mps_state* s, const mps_hamiltonian* h, const mps_hamiltonian_dev** out) {
+  Workspace& w = *s->ws;
+  if (!h || h->n_terms < 0 || (h->n_terms > 0 && (!h->x_mask || !h->z_mask || !h->coeff)))
+    return fail(MPS_EINVAL, "bad Hamiltonian arrays");
+  const size_t nt = (size_t)h->n_terms;
+  if (w.host_ham && w.host_ham_c.size() == nt &&
+      (nt == 0 || (std::memcmp(w.host_ham_x.data(), h->x_mask, nt * 8) == 0 &&
+                   std::memcmp(w.host_ham_z.data(), h->z_mask, nt * 8) == 0 &&
+                   std::memcmp(w.host_ham_c.data(), h->coeff, nt * 8) == 0))) {
+    *out = w.host_ham.get();
+    return MPS_OK;
+  }
+  mps_hamiltonian_dev* hd = nullptr;
+  MPS_TRY(mps_hamiltonian_create(s->L.n, h, &hd));
+  w.host_ham.reset(hd);
+  w.host_ham_x.assign(h->x_mask, h->x_mask + nt);
+  w.host_ham_z.assign(h->z_mask, h->z_mask + nt);
+  w.host_ham_c.assign(h->coeff, h->coeff + nt);
+  *out = hd;
   return MPS_OK;
 }
 
@@ -1338,9 +1409,8 @@ mps_status mps_apply_circuit(mps_state* s, const mps_gate* gates, int32_t n_gate
                              int32_t n_theta) {
   clear_error();
   if (!s) return fail(MPS_EINVAL, "mps_apply_circuit: state is NULL");
-  mps_circuit* c = nullptr;
-  MPS_TRY(mps_circuit_create(s->L.n, gates, n_gates, &c));
-  std::unique_ptr<mps_circuit> hold(c);
+  const mps_circuit* c = nullptr;
+  MPS_TRY(host_circuit(s, gates, n_gates, &c));
   return mps_apply_circuit_dev(s, c, theta, n_theta);
 }
 
@@ -1381,7 +1451,8 @@ mps_status mps_energy_cotangent_dev(const mps_state* s, const mps_hamiltonian_de
   // dE/dB* of instance 0
   std::vector<int> d(L.n + 1);
   MPS_CU(cudaMemcpy(d.data(), s->buf.dims, (L.n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
-  const bool dev = is_device_ptr(Bbar_out);
+  bool dev = false;
+  MPS_TRY(where_is(Bbar_out, "Bbar_out", &dev));
   size_t o = 0;
   for (int q = 0; q < L.n; ++q) {
     size_t e = (size_t)d[q] * 2 * d[q + 1];
@@ -1423,7 +1494,12 @@ mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, doub
   double* lam = reinterpret_cast<double*>(take());
   int* dims = reinterpret_cast<int*>(take());
   double* one = reinterpret_cast<double*>(take());
-  const bool dev_in = is_device_ptr(A);
+  bool dev_in = false;
+  MPS_TRY(where_is(A, "mps_svd: A", &dev_in));
+  for (const void* o : {(const void*)s_out, (const void*)V_out, (const void*)W_out, (const void*)k_out}) {
+    bool od = false;
+    MPS_TRY(where_is(o, "mps_svd: an output array", &od));
+  }
   MPS_CU(cudaMemcpy(Ain, A, mn * 16, dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
   int hd[3] = {m / 2, 1, ncol / 2};
   MPS_CU(cudaMemcpy(dims, hd, sizeof(hd), cudaMemcpyHostToDevice));
@@ -1466,7 +1542,7 @@ mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, doub
     for (int r = 0; r < m; ++r) tW[(size_t)r * Kc + j] = hW[j * m + r];
   }
   auto out = [&](void* dst, const void* src, size_t b) -> mps_status {
-    MPS_CU(cudaMemcpy(dst, src, b, is_device_ptr(dst) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    MPS_CU(cudaMemcpy(dst, src, b, ptr_location(dst) == PTR_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
     return MPS_OK;
   };
   std::vector<double> hs(Kc);
@@ -1481,9 +1557,8 @@ mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, doub
 mps_status mps_energy(const mps_state* s, const mps_hamiltonian* h, double* E_out) {
   clear_error();
   if (!s || !h) return fail(MPS_EINVAL, "mps_energy: NULL argument");
-  mps_hamiltonian_dev* hd = nullptr;
-  MPS_TRY(mps_hamiltonian_create(s->L.n, h, &hd));
-  std::unique_ptr<mps_hamiltonian_dev> hold(hd);
+  const mps_hamiltonian_dev* hd = nullptr;
+  MPS_TRY(host_hamiltonian(const_cast<mps_state*>(s), h, &hd));
   return mps_energy_dev(s, hd, E_out, nullptr);
 }
 
@@ -1698,12 +1773,11 @@ mps_status mps_energy_grad(const mps_state* s0, const mps_gate* gates, int32_t n
                            double* gate_grad_out) {
   clear_error();
   if (!s0 || !h) return fail(MPS_EINVAL, "mps_energy_grad: NULL argument");
-  mps_circuit* c = nullptr;
-  MPS_TRY(mps_circuit_create(s0->L.n, gates, n_gates, &c));
-  std::unique_ptr<mps_circuit> hold_c(c);
-  mps_hamiltonian_dev* hd = nullptr;
-  MPS_TRY(mps_hamiltonian_create(s0->L.n, h, &hd));
-  std::unique_ptr<mps_hamiltonian_dev> hold_h(hd);
+  mps_state* s = const_cast<mps_state*>(s0);
+  const mps_circuit* c = nullptr;
+  MPS_TRY(host_circuit(s, gates, n_gates, &c));
+  const mps_hamiltonian_dev* hd = nullptr;
+  MPS_TRY(host_hamiltonian(s, h, &hd));
   return mps_energy_grad_dev(s0, c, theta, n_theta, hd, E_out, grad_out, gate_grad_out);
 }
 

@@ -73,14 +73,8 @@ mps_status scratch_base(void** out) {
   return MPS_OK;
 }
 
-bool on_device(const void* p) {
-  cudaPointerAttributes a{};
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+// device (or managed) memory that the current device may use; memory of another GPU is refused
+bool on_device(const void* p) { return mpsi::ptr_location(p) == mpsi::PTR_DEVICE; }
 
 // row-major input -> column-major working copy; dims, lambda_left = 1, status = 0
 __global__ void na_prepare(const double2* __restrict__ A, int m, int n, View v) {
@@ -128,7 +122,7 @@ extern "C" mps_status mps_svd_noalloc(int32_t m, int32_t ncol, const double* A, 
                                       " (size of the library's fixed scratch array)");
   if (D < 1 || !(eps >= 0.0)) return mpsi::fail(MPS_EINVAL, "mps_svd_noalloc: bad D or eps");
   if (!on_device(A) || !on_device(s_out) || !on_device(V_out) || !on_device(W_out) || !on_device(k_out))
-    return mpsi::fail(MPS_EINVAL, "mps_svd_noalloc: every array must be device memory");
+    return mpsi::fail(MPS_EINVAL, "mps_svd_noalloc: every array must be device memory of the current device");
   void* base = nullptr;
   mps_status st = scratch_base(&base);
   if (st != MPS_OK) return st;

@@ -539,3 +539,64 @@ def test_config2_prefix_parameter_shift_on_eight_gate_angles(M):
         M.apply_circuit(stb, M.Circuit(p.n, g2), rows)
         E = M.energy(stb, ham)
         assert abs(0.5 * (E[0] - E[1]) - gg[t]) <= 1e-8 * max(1.0, np.abs(gg).max())
+
+
+# ---- the host-argument entry points of the boundary (gate list and Hamiltonian per call) --------
+
+@pytest.mark.parametrize("case", ["cfg0", "cfg1_prefix"])
+def test_host_argument_entry_points_match_the_oracle(M, case):
+    """mps_apply_circuit, mps_energy and mps_energy_grad with host mps_gate / mps_hamiltonian
+    arrays, against the oracle; repeated calls reuse the uploads (and the captured graph) and give
+    the same bits; new angles through the same uploads stay correct."""
+    import torch
+    p = S.make_problem(0 if case == "cfg0" else 1)
+    excs = p.excitations if case == "cfg0" else p.excitations[:14]
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    gates = M.compile_excitations(p.n, excs)
+    th = p.theta[: len(excs)]
+    r, og, oh = oracle(p, excs)
+    st = M.State.product(p.bits, p.spec.D, p.spec.eps, stream=torch.cuda.Stream())
+    res = [M.energy_grad_host(st, gates, th, x, z, c, gate_grad=True) for _ in range(3)]
+    E, g, gg = res[0]
+    assert abs(E - r.E) <= E_TOL * max(1.0, abs(r.E))
+    assert np.linalg.norm(g - r.grad) <= G_TOL * max(1.0, np.linalg.norm(r.grad))
+    assert np.abs(gg - r.gate_grad).max() <= G_TOL * max(1.0, np.abs(r.gate_grad).max())
+    for E2, g2, gg2 in res[1:]:                       # eager, captured, replayed: same bits
+        assert E2 == E and np.array_equal(g2, g) and np.array_equal(gg2, gg)
+    th2 = th + 0.05
+    E3, g3 = M.energy_grad_host(st, gates, th2, x, z, c)
+    r3 = OM.energy_grad(OM.init_product(p.bits), og, th2, oh, p.spec.D, p.spec.eps)
+    assert abs(E3 - r3.E) <= E_TOL * max(1.0, abs(r3.E))
+    assert np.linalg.norm(g3 - r3.grad) <= G_TOL * max(1.0, np.linalg.norm(r3.grad))
+    # forward and energy through the host-argument calls
+    st2 = M.State.product(p.bits, p.spec.D, p.spec.eps)
+    M.apply_circuit_host(st2, gates, th)
+    Ef = M.energy_host(st2, x, z, c)
+    ref = OM.apply_circuit(OM.init_product(p.bits), og, th, p.spec.D, p.spec.eps)
+    Er = OM.energy(ref, oh)
+    assert abs(Ef - Er) <= E_TOL * max(1.0, abs(Er))
+    assert M.energy_host(st2, x, z, c) == Ef
+
+
+def test_autograd_function_with_a_batched_state(M):
+    """MPSEnergy on a 2-instance state: E has one value per instance, and backward scales each
+    instance's gradient row by its own incoming gradient."""
+    import torch
+    from paper_2211_07983_gb300.autograd import mps_energy
+    p = S.make_problem(0)
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    circ = M.Circuit(p.n, M.compile_excitations(p.n, p.excitations))
+    ham = M.Hamiltonian(p.n, x, z, c)
+    th = np.stack([p.theta, p.theta + 0.3])
+    stb = M.State.product_batch(np.stack([p.bits] * 2), p.spec.D, p.spec.eps)
+    for dev in ("cuda", "cpu"):
+        theta = torch.tensor(th, dtype=torch.float64, device=dev, requires_grad=True)
+        E = mps_energy(theta, stb, circ, ham)
+        assert E.shape == (2,)
+        (2.0 * E[0] - 5.0 * E[1]).backward()
+        E_ref, g_ref = M.energy_grad(stb, circ, th, ham)
+        assert np.abs(E.detach().cpu().numpy() - E_ref).max() < 1e-14
+        want = np.stack([2.0 * g_ref[0], -5.0 * g_ref[1]])
+        assert np.abs(theta.grad.cpu().numpy() - want).max() < 1e-13
+    with pytest.raises(ValueError):
+        mps_energy(torch.tensor(th[0], device="cuda"), stb, circ, ham)   # one row per instance needed

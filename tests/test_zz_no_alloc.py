@@ -1,8 +1,8 @@
 """mps_svd_noalloc: the gate SVD for callers that cannot allocate device memory.
 
-Some callers cannot call cudaMalloc: code running inside a CUDA-graph capture, latency-critical
-loops that cannot afford the device synchronisation an allocation implies, and embedders whose
-device memory belongs to another allocator.  The no-allocation entry point serves them from a
+Some callers cannot call cudaMalloc: embedders whose device memory belongs to another allocator
+(or to a pool sized once at start-up), and latency-critical loops that cannot afford the device
+synchronisation an allocation can imply.  The no-allocation entry point serves them from a
 fixed scratch array inside the library.  This test calls it through the C ABI on two different
 matrices in a row and checks each result against the allocating entry point mps_svd_dev.
 It lives in its own file, collected last.
