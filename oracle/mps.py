@@ -22,7 +22,8 @@ Readings:
 * The gradient is the exact derivative of this truncated forward pass with the
   kept count k held fixed (the "local" approach of Sec. 4 made exact): the SVD is
   differentiated through M = C~^+ C~ = V diag(s^2) V^+ with the full spectrum,
-  F_ij = 1/(w_j - w_i), set to 0 for pairs degenerate to within 1e-10 (DEGEN_REL);
+  F_ij = 1/(w_j - w_i), set to 0 for pairs degenerate to within 1e-10 relative (DEGEN_REL)
+  or closer than 1e-13 s_1 (DEGEN_ABS);
   singular values at or below 1e-13 s_1 count as exact zeros (NULL_REL).
 """
 from __future__ import annotations
@@ -38,6 +39,11 @@ from . import pauli
 # exactly degenerate: their F_ij is 0.  A rotation inside an exactly degenerate block leaves
 # E unchanged, and a singular-value split at rounding level must not be divided by.
 DEGEN_REL = 1e-10
+# A computed singular value is known to an absolute accuracy of a few ulps of s_1, so two values
+# closer than DEGEN_ABS * s_1 are indistinguishable from an exactly degenerate pair as well; for
+# values far below s_1 this absolute rule is the one that applies (a degenerate pair at 5e-11 s_1
+# comes out split by ~1e-16 s_1, i.e. 2e-6 relative, which the relative rule alone would divide by).
+DEGEN_ABS = 1e-13
 # Singular values at or below NULL_REL * s_1 are rounding noise of an exactly rank-deficient
 # matrix (particle-number and spin symmetry make many two-site tensors rank deficient); the
 # adjoint treats them as exact zeros: w_i = 0 and the column (C~ V)_i = 0.
@@ -250,15 +256,19 @@ def svd_adjoint(Cm, s, V, k, sbar_k, Vbar_k):
     ncol = V.shape[0]
     w = np.zeros(ncol)
     w[: len(s)] = s * s
+    sv = np.zeros(ncol)
+    sv[: len(s)] = s
     null = np.ones(ncol, dtype=bool)
     null[: len(s)] = s <= NULL_REL * s[0]
     w[null] = 0.0
+    sv[null] = 0.0
     wbar = np.zeros(ncol)
     wbar[:k] = sbar_k / (2.0 * s[:k])
     Vbar = np.zeros((ncol, ncol), dtype=complex)
     Vbar[:, :k] = Vbar_k
     dw = w[None, :] - w[:, None]                  # dw[i, j] = w_j - w_i
-    big = np.abs(dw) > DEGEN_REL * np.maximum(w[None, :], w[:, None])
+    big = (np.abs(dw) > DEGEN_REL * np.maximum(w[None, :], w[:, None])) & \
+          (np.abs(sv[None, :] - sv[:, None]) > DEGEN_ABS * s[0])
     F = np.where(big, 1.0 / np.where(big, dw, 1.0), 0.0)   # diagonal: dw = 0 -> 0
     J = F * (V.conj().T @ Vbar)
     W = Cm @ V
