@@ -270,6 +270,18 @@ mps_status mps_svd_noalloc(int32_t m, int32_t ncol, const double* A, int32_t D, 
                            double* V_out, double* W_out, int32_t* k_out, void* cuda_stream);
 
 /*
+ * One complex GEMM C = op(A) op(B) (M x N, inner size K) through the kernels of the contractions,
+ * for testing them on their own; the paper has no counterpart.  op codes: 0 N, 1 T (transpose),
+ * 2 H (conjugate transpose), 3 C (conjugate).  A, B, C: device memory of the current device,
+ * row-major, interleaved (re, im), leading dimensions lda, ldb, ldc in complex elements; C is
+ * overwritten.  engine: 0 = split-TF32 on mma.sync tensor-core instructions, 1 = split-TF32 on
+ * tcgen05.mma with tensor-memory accumulators (the mixed path's large sweep contractions), 2 =
+ * FP64 (the FP64 path's kernel).  Uses the default stream and synchronises.
+ */
+mps_status mps_zgemm_mixed_dev(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda, int32_t opA,
+                               const double* B, int32_t ldb, int32_t opB, double* C, int32_t ldc, int32_t engine);
+
+/*
  * Profiling of the gate SVD, the dominant kernel.  While enabled, every SVD launch of calls on
  * this state is bracketed by CUDA events on the state's stream and the SVD kernel adds the
  * floating-point operations its sweeps actually performed to a device counter.

@@ -76,6 +76,8 @@ _SIGS = {
                                       c_void_p]),
     "mps_svd_dev": (c_int32, [c_int32, c_int32, c_void_p, c_int32, c_double, c_void_p, c_void_p, c_void_p,
                               c_void_p]),
+    "mps_zgemm_mixed_dev": (c_int32, [c_int32, c_int32, c_int32, c_void_p, c_int32, c_int32, c_void_p, c_int32,
+                                      c_int32, c_void_p, c_int32, c_int32]),
     "mps_profile": (c_int32, [c_void_p, c_int32]),
     "mps_profile_read": (c_int32, [c_void_p, c_void_p]),
     "mps_profile_svd_phases": (c_int32, [c_void_p, c_void_p]),

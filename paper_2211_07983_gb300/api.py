@@ -353,5 +353,27 @@ def svd(A: np.ndarray, D: int, eps: float):
     return s, V, W, int(k[0])
 
 
+_OPS = {"N": 0, "T": 1, "H": 2, "C": 3}
+_ENGINES = {"mma_sync": 0, "tcgen05": 1, "fp64": 2}
+
+
+def zgemm(A, B, opA: str = "N", opB: str = "N", engine: str = "tcgen05"):
+    """mps_zgemm_mixed_dev: C = op(A) op(B) on the GPU with one of the contraction kernels.
+
+    A, B: complex128 CUDA tensors (2-d, row-major); returns C as a complex128 CUDA tensor.
+    """
+    import torch
+    M = A.shape[0] if opA in ("N", "C") else A.shape[1]
+    K = A.shape[1] if opA in ("N", "C") else A.shape[0]
+    N = B.shape[1] if opB in ("N", "C") else B.shape[0]
+    A = A.contiguous()
+    B = B.contiguous()
+    C = torch.zeros((M, N), dtype=torch.complex128, device=A.device)
+    check(_lib.load().mps_zgemm_mixed_dev(M, N, K, ctypes.c_void_p(A.data_ptr()), A.shape[1], _OPS[opA],
+                                          ctypes.c_void_p(B.data_ptr()), B.shape[1], _OPS[opB],
+                                          ctypes.c_void_p(C.data_ptr()), N, _ENGINES[engine]))
+    return C
+
+
 def kernel_launches() -> int:
     return int(_lib.load().mps_kernel_launches())

@@ -14,9 +14,10 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmps.so")
+PEAKS_OUT = os.path.join(HERE, "libpeaks.so")   # arithmetic peak microbenchmarks (roofline denominators)
 BUILD = os.path.join(HERE, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-CU_SOURCES = ["mps_api.cu", "gemm.cu", "gate_kernels.cu", "energy_kernels.cu", "noalloc.cu", "arena.cu", "gemm_tf32.cu"]
+CU_SOURCES = ["mps_api.cu", "gemm.cu", "gate_kernels.cu", "energy_kernels.cu", "noalloc.cu", "arena.cu", "gemm_tf32.cu", "svd_coop.cu", "gemm_tc.cu"]
 CXX_SOURCES = ["host_builders.cpp"]
 
 
@@ -57,10 +58,13 @@ def build(verbose: bool = False, force: bool = False) -> str:
         objs.append(o)
         jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", "-c", os.path.join(CSRC, f),
                      "-o", o])
-    if not force and not _stale(objs, CU_SOURCES + CXX_SOURCES):
+    peaks_job = [nvcc, "-std=c++17", "-O3", ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
+                 os.path.join(CSRC, "peaks.cu"), "-o", PEAKS_OUT + ".tmp"]
+    if not force and not _stale(objs, CU_SOURCES + CXX_SOURCES) and os.path.exists(PEAKS_OUT):
         return OUT
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
-        logs = list(ex.map(_run, jobs))
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs) + 1)) as ex:
+        logs = list(ex.map(_run, jobs + [peaks_job]))
+    os.replace(PEAKS_OUT + ".tmp", PEAKS_OUT)
     if verbose:
         for lg in logs:
             sys.stdout.write(lg)

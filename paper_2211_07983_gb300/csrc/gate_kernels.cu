@@ -124,6 +124,7 @@ constexpr int SVD_THREADS = 512;
 constexpr int SVD_MAX_SWEEPS = 60;
 constexpr double SVD_NULL_REL = 1e-13;   // numerical-zero singular values (relative to s_max)
 constexpr double SVD_DEGEN_REL = 1e-10;  // exactly degenerate pairs of squared singular values
+constexpr double SVD_DEGEN_ABS = 1e-13;  // pairs of singular values closer than this times s_1
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -557,9 +558,14 @@ __global__ void build_K_kernel(const double2* __restrict__ Y, const double* __re
   // numerical zeros (s <= SVD_NULL_REL s_1) enter as exact zeros
   const double wi = s[i] > SVD_NULL_REL * s[0] ? s[i] * s[i] : 0.0;
   const double wj = s[j] > SVD_NULL_REL * s[0] ? s[j] * s[j] : 0.0;
-  // F_ij = 1/(w_j - w_i), 0 inside exactly degenerate pairs (|dw| <= SVD_DEGEN_REL max(w))
+  // F_ij = 1/(w_j - w_i), 0 inside degenerate pairs: |dw| <= SVD_DEGEN_REL max(w), or singular
+  // values closer than SVD_DEGEN_ABS s_1 (a computed singular value is known to a few ulps of s_1,
+  // so a degenerate pair far below s_1 comes out split by rounding that the relative rule alone
+  // would divide by)
   const double dw = wj - wi;
-  const double F = fabs(dw) > SVD_DEGEN_REL * fmax(wi, wj) ? 1.0 / dw : 0.0;
+  const double si = wi > 0.0 ? s[i] : 0.0, sj = wj > 0.0 ? s[j] : 0.0;
+  const bool split = fabs(dw) > SVD_DEGEN_REL * fmax(wi, wj) && fabs(sj - si) > SVD_DEGEN_ABS * s[0];
+  const double F = split ? 1.0 / dw : 0.0;
   double2 v = make_double2(i == j ? wbar[i] : 0.0, 0.0);
   if (i != j) {
     if (j < k) v = cadd(v, cscale(Y[(size_t)i * k + j], F));               // J_ij = F_ij Y_ij

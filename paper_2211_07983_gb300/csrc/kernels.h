@@ -33,6 +33,16 @@ void launch_zgemm_tf32x3_small(const Batch& bt, const GemmBatch& b, int max_m, i
 void launch_zgemm_tf32x3_batched(const Batch& bt, const GemmDesc* d_descs, int count, int max_m, int max_n,
                                  cudaStream_t st);
 
+// The same batched GEMM on the 5th-generation tensor cores (tcgen05.mma kind::tf32, accumulators in
+// tensor memory), split-TF32, 128 x 128 tiles (gemm_tc.cu); `status` is the per-instance status
+// word (a bounded wait that gives up records MPS_ETIMEOUT).  zgemm_tc_available() is false when the
+// kernel's shared memory cannot be configured.
+bool zgemm_tc_available();
+void launch_zgemm_tc_batched(const Batch& bt, const GemmDesc* d_descs, int count, int max_m, int max_n, int* status,
+                             cudaStream_t st);
+// Batched GEMM steps of the mixed path use the tcgen05 kernel when both output sides can reach this
+constexpr int TC_MIN_SIDE = 64;
+
 // G (16 complex per gate) and dG/dphi from the gate table and theta (device).
 void launch_gate_matrices(const Batch& bt, const void* d_gates, int n_gates, const double* d_theta, int n_theta,
                           double2* G, double2* dG, int* status, cudaStream_t st);
@@ -84,6 +94,14 @@ size_t svd_smem_bytes(int m_cap, int n_cap);
 bool svd_fits_smem(int m_cap, int n_cap);
 // one CTA per instance
 void launch_svd(const Batch& bt, const SvdArgs& a, int m_cap, int n_cap, cudaStream_t st);
+// The same SVD of one large matrix (one instance) over the whole GPU: a cooperative launch of one
+// CTA per SM with bounded grid barriers between Jacobi rounds (svd_coop.cu), FP64 sweeps.  scratch:
+// svd_coop_scratch_bytes(m_cap, n_cap) bytes of device memory; a.scratch is not used.
+size_t svd_coop_scratch_bytes(int m_cap, int n_cap);
+cudaError_t launch_svd_coop(const SvdArgs& a, void* scratch, int m_cap, int n_cap, cudaStream_t st);
+// Gates whose two-site matrix can exceed this many rows or columns use the cooperative SVD when the
+// state holds one instance (batched states keep one CTA per instance).
+constexpr int SVD_COOP_MIN_SIDE = 129;
 
 // B_{b+1} <- (Vs[:, :k])^H reshaped [k][2][Dr]
 void launch_vh_rows(const Batch& bt, const double2* Vs, const int* dims, int b, double2* Br_out, int max_k,

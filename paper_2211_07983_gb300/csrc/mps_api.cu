@@ -158,6 +158,7 @@ struct TapeSlot {
 struct Workspace {
   Arena* arena;
   DevBuf A, svd, C, Vs, s;                        // forward scratch at the largest bond
+  DevBuf svdc;                                    // scratch of the cooperative (multi-SM) SVD
   DevBuf G, dG, theta, scalars, gate_grad, grad;  // per call
   StateBuf work, rec;                             // energy_grad working states
   std::vector<std::unique_ptr<StateBuf>> snaps;
@@ -225,8 +226,18 @@ struct Ctx {
   Batch bt;
 };
 
+// A gate on bond b runs the cooperative multi-SM SVD when the state holds one instance and the
+// gate's two-site matrix can exceed SVD_COOP_MIN_SIDE - 1 rows or columns.
+static bool gate_uses_coop(const Layout& L, int n_inst, int b) {
+  return n_inst == 1 && std::max(2 * L.cap[b], 2 * L.cap[b + 2]) >= SVD_COOP_MIN_SIDE;
+}
+static bool state_uses_coop(const Layout& L, int n_inst) {
+  return n_inst == 1 && 2 * L.max_cap >= SVD_COOP_MIN_SIDE;
+}
+
 static mps_status ensure_forward_scratch(const Layout& L, Workspace& w) {
   const size_t mc = 2 * (size_t)L.max_cap, nc = 2 * (size_t)L.max_cap;
+  if (state_uses_coop(L, w.arena->n)) MPS_TRY(w.svdc.ensure(svd_coop_scratch_bytes((int)mc, (int)nc)));
   MPS_TRY(w.A.ensure(mc * nc * sizeof(double2)));
   MPS_TRY(w.svd.ensure(2 * nc * nc * sizeof(double2)));   // SVD scratch if shared memory is too small
   MPS_TRY(w.C.ensure(mc * nc * sizeof(double2)));
@@ -319,7 +330,12 @@ static mps_status forward_gate(Ctx& cx, StateBuf& sb, int b, const double2* Gt, 
     }
     MPS_TRY(record_profile_event(w.ev_pool[w.ev_used], cx.st));
   }
-  launch_svd(cx.bt, a, 2 * L.cap[b], 2 * L.cap[b + 2], cx.st);
+  if (gate_uses_coop(L, cx.bt.n, b)) {
+    const cudaError_t e = launch_svd_coop(a, w.svdc.p, 2 * L.cap[b], 2 * L.cap[b + 2], cx.st);
+    if (e != cudaSuccess) return fail(MPS_ECUDA, std::string("cooperative SVD launch: ") + cudaGetErrorString(e));
+  } else {
+    launch_svd(cx.bt, a, 2 * L.cap[b], 2 * L.cap[b + 2], cx.st);
+  }
   if (w.profile) {
     MPS_TRY(record_profile_event(w.ev_pool[w.ev_used + 1], cx.st));
     w.ev_used += 2;
@@ -429,6 +445,7 @@ struct EnergyCache {
   double2* Z = nullptr;
   std::vector<double2*> RI, AR, Rsum;
   int max_site = 1;
+  size_t bytes = 0;        // device bytes of `bufs` per instance
 };
 
 }  // namespace mpsi
@@ -438,6 +455,17 @@ mps_hamiltonian_dev::~mps_hamiltonian_dev() = default;
 namespace mpsi {
 
 // Build every buffer, descriptor and step of the energy (+ cotangent) pass for one state layout.
+//
+// Memory is bounded by the widest trie level, not by the trie: only the left environment L_v of
+// every node is kept (the cotangent needs it again); the other per-node intermediates live in
+// slabs that hold one trie level (one site) and are reused level after level:
+//   T  (site-sized): T_p = L_p B_s of the parents of the level being formed
+//   X  (bond^2):     right environment of each node's subtree, X_v = c_v R^I + sum_children Y_c
+//   Y  (bond^2, two slabs by site parity): Y_v = T^R_{O_v}(X_v), read by the level above
+//   UE (site-sized): U_v = B_t X_v^T, then E_v = T_par(v) X_v^T (U is consumed first)
+// The cotangent walks the sites from right to left; at each site it finishes the right identity
+// accumulator A^R, the identity-part environment Eid and the seed of that site before the slabs
+// move on, so no level's intermediates are needed after its site is done.
 static mps_status build_energy_cache(const Layout& L, const StateBuf& sb, mps_hamiltonian_dev* h,
                                      double2* d_Bbar, EnergyCache& ec) {
   const int n = L.n;
@@ -446,8 +474,9 @@ static mps_status build_energy_cache(const Layout& L, const StateBuf& sb, mps_ha
   const std::vector<int>& cap = L.cap;
   auto sq = [&](int i) { return (size_t)cap[i] * cap[i]; };
   auto site_sz = [&](int s) { return (size_t)cap[s] * 2 * cap[s + 1]; };
+  auto level_n = [&](int s) { return (size_t)(h->site_begin[s + 1] - h->site_begin[s]); };
+  auto local = [&](int v) { return (size_t)(v - h->site_begin[h->node_site[v]]); };
   // ---- buffer plan (complex elements) ----
-  std::vector<size_t> off;
   size_t total = 0;
   auto take = [&](size_t elems) {
     size_t o = total;
@@ -473,25 +502,30 @@ static mps_status build_energy_cache(const Layout& L, const StateBuf& sb, mps_ha
   oRI[n] = o_one;
   oAR[n] = take(1);
   oRsum[n] = take(1);
-  std::vector<size_t> oL(nn), oX(nn), oE(nn), oU(nn), oY(nn), oT(nn, (size_t)-1);
-  std::vector<char> is_parent(nn, 0);
-  for (int v = 0; v < nn; ++v)
-    if (h->node_parent[v] >= 0) is_parent[h->node_parent[v]] = 1;
-  for (int v = 0; v < nn; ++v) {
-    int s = h->node_site[v];
-    oL[v] = take(sq(s + 1));
-    oX[v] = take(sq(s + 1));
-    oE[v] = take(site_sz(s));
-    oU[v] = take(site_sz(s));
-    oY[v] = take(sq(s));
-    if (is_parent[v] && s + 1 < n) oT[v] = take(site_sz(s + 1));
+  std::vector<size_t> oL(nn);
+  for (int v = 0; v < nn; ++v) oL[v] = take(sq(h->node_site[v] + 1));
+  size_t xs = 1, ys = 1, ues = 1, ts = 1;
+  for (int s = 0; s < n; ++s) {
+    xs = std::max(xs, level_n(s) * sq(s + 1));
+    ys = std::max(ys, level_n(s) * sq(s));
+    ues = std::max(ues, level_n(s) * site_sz(s));
+    if (s > 0) ts = std::max(ts, level_n(s - 1) * site_sz(s));
   }
+  const size_t o_X = take(xs), o_Y0 = take(ys), o_Y1 = take(ys), o_UE = take(ues), o_T = take(ts);
   size_t o_e = take(2 * (size_t)std::max(nt, 1));
   Arena* arena = sb.mem.arena;
   ec.bufs.arena = arena;
   MPS_TRY(ec.bufs.alloc(total * sizeof(double2)));
   double2* base = ec.bufs.as<double2>();
   auto P = [&](size_t o) { return base + o; };
+  // slab addresses of node v (at site s = node_site[v])
+  auto Xv = [&](int v) { return P(o_X + local(v) * sq(h->node_site[v] + 1)); };
+  auto Yv = [&](int v) {
+    const int s = h->node_site[v];
+    return P(((s & 1) ? o_Y1 : o_Y0) + local(v) * sq(s));
+  };
+  auto UEv = [&](int v) { return P(o_UE + local(v) * site_sz(h->node_site[v])); };
+  auto Tp = [&](int p) { return P(o_T + local(p) * site_sz(h->node_site[p] + 1)); };   // T of parent p
   double2 one_val = make_double2(1.0, 0.0);
   for (int i = 0; i < arena->n; ++i)
     MPS_CU(cudaMemcpy(ish(P(o_one), (size_t)i * arena->stride), &one_val, sizeof(double2), cudaMemcpyHostToDevice));
@@ -508,6 +542,7 @@ static mps_status build_energy_cache(const Layout& L, const StateBuf& sb, mps_ha
   }
   ec.max_site = 1;
   for (int s = 0; s < n; ++s) ec.max_site = std::max<int>(ec.max_site, cap[s] * cap[s + 1]);
+  ec.bytes = total * sizeof(double2);
 
   // ---- descriptors and steps ----
   std::vector<GemmDesc> D;
@@ -518,19 +553,23 @@ static mps_status build_energy_cache(const Layout& L, const StateBuf& sb, mps_ha
   auto Bs = [&](int s) { return (const double2*)(sb.B + L.site_off[s]); };
   auto OBp = [&](int s, int op) -> const double2* { return op == 0 ? Bs(s) : P(oOB[3 * s + op - 1]); };
   auto gemm_step = [&](std::vector<Step>& plan, size_t first, int mm, int mn) {
-    Step st{Step::GEMM};
-    st.off = (int)first;
-    st.count = (int)(D.size() - first);
-    st.max_m = mm;
-    st.max_n = mn;
-    if (st.count > 0) plan.push_back(st);
+    for (size_t c0 = first; c0 < D.size(); c0 += 65535) {   // grid z limit per launch
+      Step st{Step::GEMM};
+      st.off = (int)c0;
+      st.count = (int)std::min<size_t>(65535, D.size() - c0);
+      st.max_m = mm;
+      st.max_n = mn;
+      plan.push_back(st);
+    }
   };
   auto axpy_step = [&](std::vector<Step>& plan, size_t first, int max_elems) {
-    Step st{Step::AXPY};
-    st.off = (int)first;
-    st.count = (int)(AX.size() - first);
-    st.max_m = max_elems;
-    if (st.count > 0) plan.push_back(st);
+    for (size_t c0 = first; c0 < AX.size(); c0 += 65535) {
+      Step st{Step::AXPY};
+      st.off = (int)c0;
+      st.count = (int)std::min<size_t>(65535, AX.size() - c0);
+      st.max_m = max_elems;
+      plan.push_back(st);
+    }
   };
   std::vector<Step>& PE = ec.plan_e;
   std::vector<Step>& PS = ec.plan_seed;
@@ -556,25 +595,30 @@ static mps_status build_energy_cache(const Layout& L, const StateBuf& sb, mps_ha
                           dref(r + 1, 2), dref(r + 1, 2), dref(r)));
     gemm_step(PE, f, std::max(cap[s + 1], cap[r]), std::max(cap[s + 1], cap[r]));
   }
-  // trie forward sweep, site by site
-  auto Tpar = [&](int v) -> double2* {
-    int p = h->node_parent[v];
-    return p < 0 ? P(oTL[h->node_site[v]]) : P(oT[p]);
-  };
-  for (int s = 0; s < n; ++s) {
+  // T of the parents of the nodes at site s: T_p = L_p B_s (into the T slab)
+  auto parents_T = [&](std::vector<Step>& plan, int s) {
     int v0 = h->site_begin[s], v1 = h->site_begin[s + 1];
-    if (v0 == v1) continue;
     size_t f = D.size();
     std::vector<char> done(nn, 0);
     for (int v = v0; v < v1; ++v) {
       int p = h->node_parent[v];
       if (p < 0 || done[p]) continue;
       done[p] = 1;
-      D.push_back(make_desc(dims, P(oL[p]), OP_N, Bs(s), OP_N, P(oT[p]), dref(s), dref(s + 1, 2), dref(s), dref(s),
+      D.push_back(make_desc(dims, P(oL[p]), OP_N, Bs(s), OP_N, Tp(p), dref(s), dref(s + 1, 2), dref(s), dref(s),
                             dref(s + 1, 2), dref(s + 1, 2)));
     }
-    gemm_step(PE, f, cap[s], 2 * cap[s + 1]);
-    f = D.size();
+    gemm_step(plan, f, cap[s], 2 * cap[s + 1]);
+  };
+  auto Tpar = [&](int v) -> double2* {
+    int p = h->node_parent[v];
+    return p < 0 ? P(oTL[h->node_site[v]]) : Tp(p);
+  };
+  // trie forward sweep, site by site: L_v = (O_v B_s)^H T_par(v)
+  for (int s = 0; s < n; ++s) {
+    int v0 = h->site_begin[s], v1 = h->site_begin[s + 1];
+    if (v0 == v1) continue;
+    parents_T(PE, s);
+    size_t f = D.size();
     for (int v = v0; v < v1; ++v)
       D.push_back(make_desc(dims, OBp(s, h->node_op[v]), OP_H, Tpar(v), OP_N, P(oL[v]), dref(s + 1), dref(s + 1),
                             dref(s, 2), dref(s + 1), dref(s + 1), dref(s + 1)));
@@ -594,68 +638,6 @@ static mps_status build_energy_cache(const Layout& L, const StateBuf& sb, mps_ha
   PE.push_back(Step{Step::SUM});
 
   // ---- cotangent ----
-  // X_v = c_v R^I_{s+1} + sum_children Y_child;  Y_c = T^R_{O_c}(X_c)
-  for (int t = n - 1; t >= 0; --t) {
-    int v0 = h->site_begin[t], v1 = h->site_begin[t + 1];
-    if (v0 == v1) continue;
-    size_t fa = AX.size();
-    for (int v = v0; v < v1; ++v) {
-      AxpyList a{};
-      a.out = P(oX[v]);
-      a.src_begin = (int)SRC.size();
-      if (h->node_is_end[v]) {
-        SRC.push_back(P(oRI[t + 1]));
-        SRCC.push_back(h->node_end_coeff[v]);
-      }
-      for (int e = h->child_off[v]; e < h->child_off[v + 1]; ++e) {
-        SRC.push_back(P(oY[h->child_idx[e]]));
-        SRCC.push_back(1.0);
-      }
-      a.src_end = (int)SRC.size();
-      a.didx = t + 1;
-      a.mult = 1;
-      a.accumulate = 0;
-      AX.push_back(a);
-    }
-    axpy_step(PS, fa, cap[t + 1] * cap[t + 1]);
-    if (t == 0) continue;
-    size_t f = D.size();
-    for (int v = v0; v < v1; ++v)
-      D.push_back(make_desc(dims, Bs(t), OP_N, P(oX[v]), OP_T, P(oU[v]), dref(t, 2), dref(t + 1), dref(t + 1),
-                            dref(t + 1), dref(t + 1), dref(t + 1)));
-    gemm_step(PS, f, 2 * cap[t], cap[t + 1]);
-    f = D.size();
-    for (int v = v0; v < v1; ++v)
-      D.push_back(make_desc(dims, OBp(t, h->node_op[v]), OP_C, P(oU[v]), OP_T, P(oY[v]), dref(t), dref(t),
-                            dref(t + 1, 2), dref(t + 1, 2), dref(t + 1, 2), dref(t)));
-    gemm_step(PS, f, cap[t], cap[t]);
-  }
-  // A^R_t = T^R_I(A^R_{t+1}) + sum_{roots at t} Y_root,  t = n-1 .. 1 (A^R_n = 0)
-  for (int t = n - 1; t >= 1; --t) {
-    size_t f = D.size();
-    D.push_back(make_desc(dims, Bs(t), OP_N, P(oAR[t + 1]), OP_T, P(oURa[t]), dref(t, 2), dref(t + 1), dref(t + 1),
-                          dref(t + 1), dref(t + 1), dref(t + 1)));
-    gemm_step(PS, f, 2 * cap[t], cap[t + 1]);
-    f = D.size();
-    D.push_back(make_desc(dims, Bs(t), OP_C, P(oURa[t]), OP_T, P(oAR[t]), dref(t), dref(t), dref(t + 1, 2),
-                          dref(t + 1, 2), dref(t + 1, 2), dref(t)));
-    gemm_step(PS, f, cap[t], cap[t]);
-    size_t fa = AX.size();
-    AxpyList a{};
-    a.out = P(oAR[t]);
-    a.src_begin = (int)SRC.size();
-    for (int v = h->site_begin[t]; v < h->site_begin[t + 1]; ++v)
-      if (h->node_parent[v] < 0) {
-        SRC.push_back(P(oY[v]));
-        SRCC.push_back(1.0);
-      }
-    a.src_end = (int)SRC.size();
-    a.didx = t;
-    a.mult = 1;
-    a.accumulate = 1;
-    if (a.src_end > a.src_begin) AX.push_back(a);
-    axpy_step(PS, fa, cap[t] * cap[t]);
-  }
   // A^L_s = T_I(A^L_{s-1}) + sum_{strings ending at s} c L_leaf;  TA_s = A^L_{s-1} B_s
   for (int s = 0; s < n; ++s) {
     size_t f = D.size();
@@ -684,50 +666,105 @@ static mps_status build_energy_cache(const Layout& L, const StateBuf& sb, mps_ha
     if (a.src_end > a.src_begin) AX.push_back(a);
     axpy_step(PS, fa, cap[s + 1] * cap[s + 1]);
   }
-  // Rsum_s = A^R_s + (c0 - E) R^I_s
-  for (int s = 1; s <= n; ++s) {
-    Step st{Step::RSUM};
-    st.slot = s;
-    st.max_m = cap[s] * cap[s];
-    PS.push_back(st);
-  }
-  // Eid_s = TA_s R^I_{s+1}^T + TL_s Rsum_{s+1}^T
-  {
-    size_t f = D.size();
-    int mm = 1, mn = 1;
-    for (int s = 0; s < n; ++s) {
-      D.push_back(make_desc(dims, P(oTA[s]), OP_N, P(oRI[s + 1]), OP_T, P(oEid[s]), dref(s, 2), dref(s + 1),
-                            dref(s + 1), dref(s + 1), dref(s + 1), dref(s + 1)));
-      mm = std::max(mm, 2 * cap[s]);
-      mn = std::max(mn, cap[s + 1]);
+  // right to left, one site per iteration
+  for (int t = n - 1; t >= 0; --t) {
+    const int v0 = h->site_begin[t], v1 = h->site_begin[t + 1];
+    // X_v = c_v R^I_{t+1} + sum_children Y_child
+    if (v1 > v0) {
+      size_t fa = AX.size();
+      for (int v = v0; v < v1; ++v) {
+        AxpyList a{};
+        a.out = Xv(v);
+        a.src_begin = (int)SRC.size();
+        if (h->node_is_end[v]) {
+          SRC.push_back(P(oRI[t + 1]));
+          SRCC.push_back(h->node_end_coeff[v]);
+        }
+        for (int e = h->child_off[v]; e < h->child_off[v + 1]; ++e) {
+          SRC.push_back(Yv(h->child_idx[e]));
+          SRCC.push_back(1.0);
+        }
+        a.src_end = (int)SRC.size();
+        a.didx = t + 1;
+        a.mult = 1;
+        a.accumulate = 0;
+        AX.push_back(a);
+      }
+      axpy_step(PS, fa, cap[t + 1] * cap[t + 1]);
     }
-    gemm_step(PS, f, mm, mn);
-    f = D.size();
-    for (int s = 0; s < n; ++s)
-      D.push_back(make_desc(dims, P(oTL[s]), OP_N, P(oRsum[s + 1]), OP_T, P(oEid[s]), dref(s, 2), dref(s + 1),
-                            dref(s + 1), dref(s + 1), dref(s + 1), dref(s + 1), true));
-    gemm_step(PS, f, mm, mn);
-    // E_v = T_par(v) X_v^T for every node
-    f = D.size();
-    for (int v = 0; v < nn; ++v) {
-      int s = h->node_site[v];
-      D.push_back(make_desc(dims, Tpar(v), OP_N, P(oX[v]), OP_T, P(oE[v]), dref(s, 2), dref(s + 1), dref(s + 1),
-                            dref(s + 1), dref(s + 1), dref(s + 1)));
+    if (t > 0 && v1 > v0) {
+      // Y_v = T^R_{O_v}(X_v): U_v = B_t X_v^T, Y_v = conj(O_v B_t) U_v^T
+      size_t f = D.size();
+      for (int v = v0; v < v1; ++v)
+        D.push_back(make_desc(dims, Bs(t), OP_N, Xv(v), OP_T, UEv(v), dref(t, 2), dref(t + 1), dref(t + 1),
+                              dref(t + 1), dref(t + 1), dref(t + 1)));
+      gemm_step(PS, f, 2 * cap[t], cap[t + 1]);
+      f = D.size();
+      for (int v = v0; v < v1; ++v)
+        D.push_back(make_desc(dims, OBp(t, h->node_op[v]), OP_C, UEv(v), OP_T, Yv(v), dref(t), dref(t),
+                              dref(t + 1, 2), dref(t + 1, 2), dref(t + 1, 2), dref(t)));
+      gemm_step(PS, f, cap[t], cap[t]);
     }
-    // launched in chunks of 65535 (grid z limit)
-    for (size_t c0 = f; c0 < D.size(); c0 += 65535) {
-      Step st{Step::GEMM};
-      st.off = (int)c0;
-      st.count = (int)std::min<size_t>(65535, D.size() - c0);
-      st.max_m = mm;
-      st.max_n = mn;
+    if (t >= 1) {
+      // A^R_t = T^R_I(A^R_{t+1}) + sum_{roots at t} Y_root
+      size_t f = D.size();
+      D.push_back(make_desc(dims, Bs(t), OP_N, P(oAR[t + 1]), OP_T, P(oURa[t]), dref(t, 2), dref(t + 1),
+                            dref(t + 1), dref(t + 1), dref(t + 1), dref(t + 1)));
+      gemm_step(PS, f, 2 * cap[t], cap[t + 1]);
+      f = D.size();
+      D.push_back(make_desc(dims, Bs(t), OP_C, P(oURa[t]), OP_T, P(oAR[t]), dref(t), dref(t), dref(t + 1, 2),
+                            dref(t + 1, 2), dref(t + 1, 2), dref(t)));
+      gemm_step(PS, f, cap[t], cap[t]);
+      size_t fa = AX.size();
+      AxpyList a{};
+      a.out = P(oAR[t]);
+      a.src_begin = (int)SRC.size();
+      for (int v = v0; v < v1; ++v)
+        if (h->node_parent[v] < 0) {
+          SRC.push_back(Yv(v));
+          SRCC.push_back(1.0);
+        }
+      a.src_end = (int)SRC.size();
+      a.didx = t;
+      a.mult = 1;
+      a.accumulate = 1;
+      if (a.src_end > a.src_begin) AX.push_back(a);
+      axpy_step(PS, fa, cap[t] * cap[t]);
+    }
+    // Rsum_{t+1} = A^R_{t+1} + (c0 - E) R^I_{t+1}
+    {
+      Step st{Step::RSUM};
+      st.slot = t + 1;
+      st.max_m = cap[t + 1] * cap[t + 1];
       PS.push_back(st);
     }
+    // Eid_t = TA_t R^I_{t+1}^T + TL_t Rsum_{t+1}^T
+    {
+      size_t f = D.size();
+      D.push_back(make_desc(dims, P(oTA[t]), OP_N, P(oRI[t + 1]), OP_T, P(oEid[t]), dref(t, 2), dref(t + 1),
+                            dref(t + 1), dref(t + 1), dref(t + 1), dref(t + 1)));
+      gemm_step(PS, f, 2 * cap[t], cap[t + 1]);
+      f = D.size();
+      D.push_back(make_desc(dims, P(oTL[t]), OP_N, P(oRsum[t + 1]), OP_T, P(oEid[t]), dref(t, 2), dref(t + 1),
+                            dref(t + 1), dref(t + 1), dref(t + 1), dref(t + 1), true));
+      gemm_step(PS, f, 2 * cap[t], cap[t + 1]);
+    }
+    if (v1 > v0) {
+      // E_v = T_par(v) X_v^T (T of the parents recomputed into the T slab)
+      parents_T(PS, t);
+      size_t f = D.size();
+      for (int v = v0; v < v1; ++v)
+        D.push_back(make_desc(dims, Tpar(v), OP_N, Xv(v), OP_T, UEv(v), dref(t, 2), dref(t + 1), dref(t + 1),
+                              dref(t + 1), dref(t + 1), dref(t + 1)));
+      gemm_step(PS, f, 2 * cap[t], cap[t + 1]);
+    }
+    Step st{Step::SEED};
+    st.slot = t;
+    PS.push_back(st);
   }
-  PS.push_back(Step{Step::SEED});
   std::vector<SeedSite> seeds(n);
   std::vector<const double2*> Enode(nn);
-  for (int v = 0; v < nn; ++v) Enode[v] = P(oE[v]);
+  for (int v = 0; v < nn; ++v) Enode[v] = UEv(v);
   for (int s = 0; s < n; ++s) {
     seeds[s].out = d_Bbar ? d_Bbar + L.site_off[s] : nullptr;
     seeds[s].Eid = P(oEid[s]);
@@ -807,7 +844,9 @@ static mps_status energy_pass_impl(const Layout& L, const StateBuf& sb, cudaStre
     for (const Step& s : plan) {
       switch (s.kind) {
         case Step::GEMM:
-          if (tf32)
+          if (tf32 && s.max_m >= TC_MIN_SIDE && s.max_n >= TC_MIN_SIDE && zgemm_tc_available())
+            launch_zgemm_tc_batched(bt, ec.d_desc + s.off, s.count, s.max_m, s.max_n, status, st);
+          else if (tf32)
             launch_zgemm_tf32x3_batched(bt, ec.d_desc + s.off, s.count, s.max_m, s.max_n, st);
           else
             launch_zgemm_batched(bt, ec.d_desc + s.off, s.count, s.max_m, s.max_n, st);
@@ -825,8 +864,8 @@ static mps_status energy_pass_impl(const Layout& L, const StateBuf& sb, cudaStre
         case Step::RSUM:
           launch_rsum(bt, ec.Rsum[s.slot], ec.AR[s.slot], ec.RI[s.slot], h->c0, d_E, sb.dims, s.slot, s.max_m, st);
           break;
-        case Step::SEED:
-          launch_seed_assemble(bt, ec.d_seed, L.n, ec.d_Enode, ec.d_nodeop, sb.dims, ec.Z, ec.max_site, st);
+        case Step::SEED:   // the seed of one site (its trie level's E slab is reused next)
+          launch_seed_assemble(bt, ec.d_seed + s.slot, 1, ec.d_Enode, ec.d_nodeop, sb.dims, ec.Z, ec.max_site, st);
           break;
       }
     }
@@ -1526,7 +1565,13 @@ mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, doub
   a.lam_left = one;
   a.lam_left_copy = nullptr;
   a.status = status.as<int>();
-  launch_svd(Batch{1, 0}, a, m, ncol, 0);
+  DevBuf coop;
+  if (std::max(m, ncol) >= SVD_COOP_MIN_SIDE) {   // the multi-SM SVD that large gates use
+    MPS_TRY(coop.alloc(svd_coop_scratch_bytes(m, ncol)));
+    MPS_CU(launch_svd_coop(a, coop.p, m, ncol, 0));
+  } else {
+    launch_svd(Batch{1, 0}, a, m, ncol, 0);
+  }
   MPS_CU(cudaGetLastError());
   MPS_CU(cudaDeviceSynchronize());
   int code = 0, k = 0;
@@ -1551,6 +1596,39 @@ mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, doub
   MPS_TRY(out(V_out, tV.data(), Kc * ncol * 16));
   MPS_TRY(out(W_out, tW.data(), Kc * m * 16));
   MPS_TRY(out(k_out, &k, sizeof(int)));
+  return MPS_OK;
+}
+
+mps_status mps_zgemm_mixed_dev(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda, int32_t opA,
+                               const double* B, int32_t ldb, int32_t opB, double* C, int32_t ldc, int32_t engine) {
+  clear_error();
+  if (!A || !B || !C) return fail(MPS_EINVAL, "mps_zgemm_mixed: NULL argument");
+  if (M < 1 || N < 1 || K < 1 || opA < 0 || opA > 3 || opB < 0 || opB > 3 || engine < 0 || engine > 2)
+    return fail(MPS_EINVAL, "mps_zgemm_mixed: bad sizes, op codes or engine");
+  if (ldc < N) return fail(MPS_EINVAL, "mps_zgemm_mixed: ldc < N");
+  if (lda < ((opA == OP_N || opA == OP_C) ? K : M) || ldb < ((opB == OP_N || opB == OP_C) ? N : K))
+    return fail(MPS_EINVAL, "mps_zgemm_mixed: leading dimension too small");
+  for (const void* q : {(const void*)A, (const void*)B, (const void*)C})
+    if (ptr_location(q) != PTR_DEVICE) return fail(MPS_EINVAL, "mps_zgemm_mixed: arrays must be device memory");
+  if (engine == 1 && !zgemm_tc_available()) return fail(MPS_ECUDA, "mps_zgemm_mixed: tcgen05 kernel unavailable");
+  GemmDesc d = make_desc(nullptr, reinterpret_cast<const double2*>(A), opA, reinterpret_cast<const double2*>(B), opB,
+                         reinterpret_cast<double2*>(C), dconst(M), dconst(N), dconst(K), dconst(lda), dconst(ldb),
+                         dconst(ldc));
+  DevBuf dd, status;
+  MPS_TRY(dd.alloc(sizeof(GemmDesc)));
+  MPS_TRY(status.alloc(sizeof(int)));
+  MPS_CU(cudaMemcpy(dd.p, &d, sizeof(GemmDesc), cudaMemcpyHostToDevice));
+  if (engine == 1)
+    launch_zgemm_tc_batched(Batch{1, 0}, dd.as<GemmDesc>(), 1, M, N, status.as<int>(), 0);
+  else if (engine == 0)
+    launch_zgemm_tf32x3_batched(Batch{1, 0}, dd.as<GemmDesc>(), 1, M, N, 0);
+  else
+    launch_zgemm_batched(Batch{1, 0}, dd.as<GemmDesc>(), 1, M, N, 0);
+  MPS_CU(cudaGetLastError());
+  MPS_CU(cudaDeviceSynchronize());
+  int code = 0;
+  MPS_CU(cudaMemcpy(&code, status.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (code) return fail((mps_status)code, "mps_zgemm_mixed: device status");
   return MPS_OK;
 }
 
@@ -1729,7 +1807,7 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
     MPS_CU(cudaGraphLaunch(w.graph_exec, s->st));
     add_launches(w.graph_kernels);
     w.ev_used = w.graph_ev_used;   // the graph re-records the profiling events of its capture
-  } else if (key == w.graph_seen && s->cfg.cuda_stream != nullptr) {
+  } else if (key == w.graph_seen && s->cfg.cuda_stream != nullptr && !state_uses_coop(L, s->n_inst())) {
     // second call with the same buffers: capture the call as a graph, then replay it
     if (w.graph_exec) {
       cudaGraphExecDestroy(w.graph_exec);

@@ -180,9 +180,11 @@ def test_invalid_arguments_are_reported(M):
 
 
 @pytest.mark.parametrize("shape,rank", [((4, 4), 2), ((8, 32), 5), ((32, 8), 8), ((64, 64), 64), ((128, 96), 40),
-                                        ((96, 128), 96), ((256, 256), 256), ((128, 512), 100)])
+                                        ((96, 128), 96), ((256, 256), 256), ((128, 512), 100), ((512, 512), 512),
+                                        ((512, 384), 300), ((256, 512), 256)])
 def test_gpu_svd_against_lapack(M, shape, rank):
-    """Steps S3-S4 on their own: singular values, orthonormal V, W = A V, truncation count."""
+    """Steps S3-S4 on their own: singular values, orthonormal V, W = A V, truncation count.
+    Shapes with a side above 128 run the cooperative multi-SM SVD (the one large gates use)."""
     rng = np.random.default_rng(sum(shape) + rank)
     m, n = shape
     A = (rng.standard_normal((m, rank)) + 1j * rng.standard_normal((m, rank))) @ (
@@ -600,3 +602,45 @@ def test_autograd_function_with_a_batched_state(M):
         assert np.abs(theta.grad.cpu().numpy() - want).max() < 1e-13
     with pytest.raises(ValueError):
         mps_energy(torch.tensor(th[0], device="cuda"), stb, circ, ham)   # one row per instance needed
+
+
+# ---- the full-size workload (n = 40, D = 256): a prefix against the oracle's stored values -----
+
+def _config4_golden():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config4_prefix.json")
+    if not os.path.exists(path):
+        pytest.skip("tests/golden/config4_prefix.json not generated (tests/golden/make_config4_prefix.py)")
+    with open(path) as f:
+        return json.load(f)
+
+
+def test_config4_prefix_against_oracle_values(M):
+    """n = 40, 20 electrons, D = 256, eps = 1e-10, the full 20k-string Hamiltonian: twelve singles
+    and five doubles of the pruned list take bonds 16-18 to D = 256 (or just below), so the
+    512 x 512 gate SVDs run on the cooperative multi-SM kernel, truncation by D happens, and the
+    reverse pass re-runs checkpoint segments of 512 gates.  E and dE/dtheta against the oracle's
+    values written by tests/golden/make_config4_prefix.py (the oracle takes about an hour on a CPU
+    for this, so its result is stored)."""
+    gold = _config4_golden()
+    p = S.make_problem(4)
+    excs = [p.excitations[t] for t in gold["prefix"]]
+    th = np.array([p.theta[t] for t in gold["prefix"]])
+    assert np.array_equal(th, np.array(gold["theta"]))
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    assert len(x) == gold["n_strings"]
+    gates = M.compile_excitations(p.n, excs)
+    assert len(gates) == gold["n_gates"]
+    circ = M.Circuit(p.n, gates)
+    ham = M.Hamiltonian(p.n, x, z, c)
+    st = M.State.product(p.bits, p.spec.D, p.spec.eps, checkpoint_every=512)
+    E, g, gg = M.energy_grad(st, circ, th, ham, gate_grad=True)
+    gE, gg_ref, g_ref = gold["E"], np.array(gold["gate_grad"]), np.array(gold["grad"])
+    assert abs(E - gE) <= E_TOL * max(1.0, abs(gE))
+    assert np.linalg.norm(g - g_ref) <= G_TOL * max(1.0, np.linalg.norm(g_ref))
+    assert np.abs(gg - gg_ref).max() <= G_TOL * max(1.0, np.abs(gg_ref).max())
+    st2 = M.State.product(p.bits, p.spec.D, p.spec.eps)
+    M.apply_circuit(st2, circ, th)
+    dims, _, _ = st2.read()
+    assert list(dims[1:-1]) == gold["bond_dims"] and max(dims) == 256
