@@ -41,11 +41,6 @@ WORKLOADS = {
     "n12_D64_p10": (1, 10),
     "n12_D64_p40": (1, 40),
 }
-# Per-SM ALU peaks used for the single-CTA SVD kernel (recipe nominal figures, per SM):
-# FP64 1.25 TFLOP/s / 152 SMs; FP32 152 SMs x 128 FMA/clk x 2 x 2.07 GHz = 80.5 TFLOP/s / 152.
-N_SM = 152
-P64_SM = 1.25e12 / N_SM
-P32_SM = 128 * 2 * 2.07e9
 
 
 def parse():
@@ -59,6 +54,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
+    ap.add_argument("--no-n40", action="store_true", help="skip the n = 40, D = 256 measurements")
     return ap.parse_args()
 
 
@@ -186,6 +182,155 @@ def run_reference(args, rank, world):
 
 
 # ---- our implementation ---------------------------------------------------------------------
+def measure_peaks():
+    """Arithmetic peaks of this GPU from libpeaks.so (FP64/FP32 FMA, TF32 mma.sync, TF32 tcgen05)."""
+    import ctypes
+    import paper_2211_07983_gb300 as M
+    lib = ctypes.CDLL(os.path.join(os.path.dirname(M.__file__), "libpeaks.so"))
+    lib.peaks_measure.argtypes = [ctypes.c_void_p]
+    lib.peaks_measure_tcgen05.argtypes = [ctypes.c_void_p]
+    o = (ctypes.c_double * 4)()
+    t = (ctypes.c_double * 2)()
+    rc1, rc2 = lib.peaks_measure(o), lib.peaks_measure_tcgen05(t)
+    return {"fp64_tflops": o[0] / 1e12, "fp32_tflops": o[1] / 1e12, "tf32_mma_sync_tflops": o[2] / 1e12,
+            "tf32_tcgen05_tflops": t[0] / 1e12, "sms": int(o[3]), "rc": [rc1, rc2],
+            "how": "libpeaks.so: register-only FMA chains (8 per thread, 8 CTAs of 256 threads per SM); "
+                   "mma.sync m16n8k8 TF32 chains; one CTA per SM issuing 128x256x8 tcgen05.mma kind::tf32 "
+                   "back to back; CUDA events, best launch of 3-5 after a warm-up"}
+
+
+def event_time(stream, fn):
+    """Device time (s) of fn() on `stream` bracketed by CUDA events."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def trie_work(x, z, n, D):
+    """Trie nodes of the canonical strings and the bond caps (2^min(i, n-i), at most D)."""
+    cap = [min(2 ** min(i, n - i), D) for i in range(n + 1)]
+    nodes = set()
+    for xm, zm in zip(x.tolist(), z.tolist()):
+        sup = xm | zm
+        if not sup:
+            continue
+        a, b = (sup & -sup).bit_length() - 1, sup.bit_length() - 1
+        sym = tuple((((xm >> q) & 1) | (((zm >> q) & 1) << 1)) for q in range(a, b + 1))
+        for e in range(1, len(sym) + 1):
+            nodes.add((a, sym[:e]))
+    return nodes, cap
+
+
+def energy_mac(nodes, dims, n):
+    """Complex MACs of one energy pass as the trie runs it: per node v at site s,
+    L_v = (O B_s)^H T_par costs 2 D_s D_{s+1}^2; T_p = L_p B_s costs 2 D_s^2 D_{s+1} once per parent
+    (shared by its children; a string's first site uses the identity chain's T); the two identity
+    chains cost 2 D_s D_{s+1} (D_s + D_{s+1}) per site each."""
+    mac = 0
+    parents = set()
+    for a, sym in nodes:
+        s = a + len(sym) - 1
+        mac += 2 * dims[s] * dims[s + 1] ** 2
+        if len(sym) > 1:
+            parents.add((a, sym[:-1]))
+    for a, sym in parents:
+        s = a + len(sym)            # the children's site
+        mac += 2 * dims[s] ** 2 * dims[s + 1]
+    mac += 2 * sum(2 * dims[q] * dims[q + 1] * (dims[q] + dims[q + 1]) for q in range(n))
+    return mac
+
+
+# the n = 40, D = 256 workload: twelve singles and five short doubles of the pruned list (the
+# prefix whose oracle values tests/golden/config4_prefix.json holds)
+N40_PREFIX = list(range(12)) + [825, 189, 824, 920, 1172]
+
+
+def run_n40(M, stream, peaks):
+    """n = 40, D = 256 on one GPU: the prefix circuit's E+grad (FP64 and mixed), the Pauli-sweep
+    energy on its final state (20083 strings), and the measured gate cost at 512 x 512."""
+    import torch
+    p = S.make_problem(4)
+    excs = [p.excitations[t] for t in N40_PREFIX]
+    th = np.array([p.theta[t] for t in N40_PREFIX])
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    gates = M.compile_excitations(p.n, excs)
+    full_gates = M.compile_excitations(p.n, p.excitations)
+    circ = M.Circuit(p.n, gates)
+    ham = M.Hamiltonian(p.n, x, z, c)
+    out = {"workload": f"n40_D256: n=40, 20 electrons, D=256, eps=1e-10, {len(x)} Pauli strings (the full Hamiltonian); "
+                       f"circuit = 12 singles + 5 doubles of the pruned excitation list ({len(gates)} gates; the "
+                       f"full list has {len(p.excitations)} excitations, {len(full_gates)} gates)"}
+    # forward with the gate SVD timed by CUDA events around every launch
+    st = M.State.product(p.bits, p.spec.D, p.spec.eps, stream=stream)
+    st.profile(True)
+    M.apply_circuit(st, circ, th)                      # warm-up (cooperative kernel set-up, plans)
+    st.free()
+    st = M.State.product(p.bits, p.spec.D, p.spec.eps, stream=stream)
+    st.profile(True)
+    st.profile_read()
+    t_fwd = event_time(stream, lambda: M.apply_circuit(st, circ, th))
+    pr = st.profile_read()
+    dims, _, _ = st.read()
+    out["forward"] = {"s": t_fwd, "gates": len(gates), "svd_ms_total": pr["svd_ms"], "svd_launches": pr["svd_launches"],
+                      "bond_dims": [int(v) for v in dims]}
+    # Pauli sweeps on the final state: FP64 and mixed (tcgen05 split-TF32 for bond sides >= 64)
+    nodes, cap = trie_work(x, z, p.n, p.spec.D)
+    mac = energy_mac(nodes, [int(v) for v in dims], p.n)
+    sweeps = {}
+    for prec in ("fp64", "mixed"):
+        s2 = M.State.product(p.bits, p.spec.D, p.spec.eps, stream=stream, precision=prec)
+        M.apply_circuit(s2, circ, th)
+        E0 = M.energy(s2, ham)                         # builds the sweep plan
+        ts = [event_time(stream, lambda: M.energy(s2, ham)) for _ in range(3)]
+        t = min(ts)
+        sweeps[prec] = {"E": E0, "s": t, "pauli_terms_per_s": len(x) / t, "complex_mac": mac,
+                        "algorithmic_tflops": 8.0 * mac / t / 1e12}
+        s2.free()
+        torch.cuda.synchronize()
+    sweeps["mixed"]["rel_E_vs_fp64"] = abs(sweeps["mixed"]["E"] - sweeps["fp64"]["E"]) / abs(sweeps["fp64"]["E"])
+    # the tensor-core work of the mixed sweeps: 4 real products per complex MAC, 3 TF32 MMAs each
+    tc_rate = 24.0 * mac / sweeps["mixed"]["s"] / 1e12
+    sweeps["mixed"]["roofline"] = {"bound": "tensor", "achieved": tc_rate, "peak": peaks["tf32_tcgen05_tflops"],
+                                   "unit": "TFLOP/s", "frac": tc_rate / peaks["tf32_tcgen05_tflops"],
+                                   "note": "TF32 tensor flops = 24 x complex MACs of the trie (split-TF32: 4 real "
+                                           "products x 3 MMAs) / CUDA-event time of the whole energy call; peak = "
+                                           "tcgen05 kind::tf32 measured by libpeaks in this run"}
+    sweeps["fp64"]["roofline"] = {"bound": "alu", "achieved": sweeps["fp64"]["algorithmic_tflops"],
+                                  "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+                                  "frac": sweeps["fp64"]["algorithmic_tflops"] / peaks["fp64_tflops"]}
+    out["pauli_sweeps"] = sweeps
+    out["trie_nodes"] = len(nodes)
+    # E + gradient of the prefix circuit (checkpoint segments of 512 gates)
+    eg = {}
+    for prec in ("fp64", "mixed"):
+        s3 = M.State.product(p.bits, p.spec.D, p.spec.eps, checkpoint_every=512, stream=stream, precision=prec)
+        res = {}
+        t = event_time(stream, lambda: res.setdefault("r", M.energy_grad(s3, circ, th, ham)))
+        E, g = res["r"]
+        eg[prec] = {"s": t, "evals_per_s": 1.0 / t, "E": E, "grad_norm": float(np.linalg.norm(g)), "grad": g}
+        s3.free()
+        torch.cuda.synchronize()
+    g64, gm = eg["fp64"].pop("grad"), eg["mixed"].pop("grad")
+    eg["mixed"]["rel_E_vs_fp64"] = abs(eg["mixed"]["E"] - eg["fp64"]["E"]) / abs(eg["fp64"]["E"])
+    eg["mixed"]["rel_grad_vs_fp64"] = float(np.linalg.norm(gm - g64) / np.linalg.norm(g64))
+    eg["mixed"]["speedup_vs_fp64"] = eg["fp64"]["s"] / eg["mixed"]["s"]
+    out["energy_grad_prefix"] = eg
+    # projection of the whole 2000-excitation circuit from the measured per-gate SVD cost
+    svd_per_gate = pr["svd_ms"] / 1e3 / max(1, pr["svd_launches"])
+    out["projection_full_circuit"] = {
+        "note": "not measured: the full circuit's forward alone repeats the measured per-gate cost for every gate; "
+                "E+grad adds a recomputation and the adjoint of each gate",
+        "gates": len(full_gates), "measured_s_per_gate_forward": t_fwd / len(gates),
+        "measured_svd_s_per_gate": svd_per_gate}
+    st.free()
+    return out
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2211_07983_gb300 as M
@@ -196,6 +341,7 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
+    peaks = measure_peaks()
     cfg, n_exc = WORKLOADS[args.workload]
     p = S.make_problem(cfg)
     excs = p.excitations if n_exc is None else p.excitations[:n_exc]
@@ -241,13 +387,7 @@ def run_ours(args, rank, world, local):
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(1.0)                   # L2 flush between timed steps
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        M.energy_grad(state, circ, thetas_d, ham, out=(E_d, g_d))
-        e1.record(stream)
-        e1.synchronize()
-        dev_ms += e0.elapsed_time(e1)
+        dev_ms += 1e3 * event_time(stream, lambda: M.energy_grad(state, circ, thetas_d, ham, out=(E_d, g_d)))
     sync_all()
     clk = clocks.stop()
     launches = M.kernel_launches() - launches0
@@ -259,6 +399,7 @@ def run_ours(args, rank, world, local):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_step = float(tt.item())
     value = B * world / t_step
+    E64, g64 = E_d.cpu().numpy().copy(), g_d.cpu().numpy().copy()
     # ---- end to end: host angles in, host E and gradient out, through the public API ----
     e2e = None
     if not args.no_e2e:
@@ -280,89 +421,71 @@ def run_ours(args, rank, world, local):
     st_f = state.clone()
     M.apply_circuit(st_f, circ, thetas_d)
     M.energy(st_f, ham)                                  # builds the sweep plan
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    n_rep = 3
-    for _ in range(n_rep):
-        M.energy(st_f, ham)
-    t_energy = (time.perf_counter() - t0) / n_rep
-    terms_per_s = len(x) * B / t_energy
+    t_energy = min(event_time(stream, lambda: M.energy(st_f, ham)) for _ in range(3))
+    dims_f, _, _ = st_f.read()
     st_f.free()
-    # algorithmic work of one energy pass (per instance): every transfer step of the sweep trie
-    # and of the two identity chains costs 2 Dl Dr (Dl + Dr) complex MACs at the bond caps
-    cap = [min(2 ** min(i, p.n - i), p.spec.D) for i in range(p.n + 1)]
-    nodes = set()
-    for xm, zm in zip(x.tolist(), z.tolist()):
-        sup = xm | zm
-        if not sup:
-            continue
-        a, b = (sup & -sup).bit_length() - 1, sup.bit_length() - 1
-        sym = tuple((((xm >> q) & 1) | (((zm >> q) & 1) << 1)) for q in range(a, b + 1))
-        for e in range(1, len(sym) + 1):
-            nodes.add((a, sym[:e]))
-    step_mac = lambda site: 2 * cap[site] * cap[site + 1] * (cap[site] + cap[site + 1])
-    mac = sum(step_mac(a + len(sym) - 1) for a, sym in nodes) + 2 * sum(step_mac(q) for q in range(p.n))
-    energy_flops = 8.0 * mac * B
-    energy_roof = {"bound": "alu", "achieved": energy_flops / t_energy / 1e12, "peak": P64_SM * N_SM / 1e12,
-                   "unit": "TFLOP/s", "frac": energy_flops / t_energy / (P64_SM * N_SM),
-                   "work": f"{len(nodes)} trie nodes + 2 x {p.n} identity steps per instance, "
-                           "2 Dl Dr (Dl + Dr) complex MACs each at the bond caps; host-clock time of the "
-                           "whole energy call"}
-    # ---- the mixed-precision path on the same instances (3xTF32 contractions and sweeps) ----
+    terms_per_s = len(x) * B / t_energy
+    nodes, cap = trie_work(x, z, p.n, p.spec.D)
+    energy_flops = 8.0 * energy_mac(nodes, [int(v) for v in dims_f], p.n) * B
+    energy_roof = {"bound": "alu", "achieved": energy_flops / t_energy / 1e12, "peak": peaks["fp64_tflops"],
+                   "unit": "TFLOP/s", "frac": energy_flops / t_energy / 1e12 / peaks["fp64_tflops"],
+                   "work": f"{len(nodes)} trie nodes per instance: L_v = (O B)^H T costs 2 Dl Dr^2 complex MACs per "
+                           "node, T = L B costs 2 Dl^2 Dr once per parent, plus the two identity chains, at instance 0's "
+                           "final bond dimensions; CUDA-event time of the whole energy call; peak = FP64 FMA "
+                           "measured by libpeaks in this run"}
+    # ---- the mixed-precision path on the same instances ----
     mixed = None
+    state.free()
+    torch.cuda.synchronize()
     if not args.no_mixed:
-        E64, g64 = E_d.cpu().numpy().copy(), g_d.cpu().numpy().copy()
-        state.free()
-        torch.cuda.synchronize()
         st_m = M.State.product_batch(np.stack([p.bits] * B), p.spec.D, p.spec.eps, checkpoint_every=0,
                                      stream=stream, precision="mixed")
         for _ in range(2):                      # eager, then captured
             M.energy_grad(st_m, circ, thetas_d, ham, out=(E_d, g_d))
         torch.cuda.synchronize()
         ms_m = 0.0
-        n_m = max(5, min(args.steps, 5))        # five timed steps
+        n_m = 5
         for _ in range(n_m):
             with torch.cuda.stream(stream):
                 flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            M.energy_grad(st_m, circ, thetas_d, ham, out=(E_d, g_d))
-            e1.record(stream)
-            e1.synchronize()
-            ms_m += e0.elapsed_time(e1)
+            ms_m += 1e3 * event_time(stream, lambda: M.energy_grad(st_m, circ, thetas_d, ham, out=(E_d, g_d)))
         Em, gm = E_d.cpu().numpy(), g_d.cpu().numpy()
         t_m = ms_m / 1e3 / n_m
         g_rel = np.linalg.norm(gm - g64, axis=1) / np.maximum(1.0, np.linalg.norm(g64, axis=1))
-        mixed = {"value": B * world / t_m, "unit": "evals/s", "ms_per_step": 1e3 * t_m,
+        mixed = {"value": B * world / t_m, "unit": "evals/s", "ms_per_step": 1e3 * t_m, "steps": n_m,
                  "speedup_vs_fp64": t_step / t_m,
                  "max_rel_E_err_vs_fp64": float(np.max(np.abs(Em - E64) / np.maximum(1.0, np.abs(E64)))),
                  "rel_grad_err_vs_fp64": {"median": float(np.median(g_rel)),
                                           "p90": float(np.percentile(g_rel, 90)), "max": float(g_rel.max()),
+                                          "argmax": int(g_rel.argmax()),
                                           "fraction_within_1e-5": float(np.mean(g_rel <= 1e-5))},
-                 "grad_note": "large differences come from rare ill-conditioned instances that keep Schmidt "
-                              "values just above eps",
-                 "precision": "energy Pauli sweeps and recomputed two-site tensors in 3xTF32 on tensor cores "
-                              "(mma.sync, FP32 accumulation); gate contractions, energy cotangent, SVD, SVD "
-                              "adjoint, sums FP64"}
+                 "precision": "energy Pauli sweeps and recomputed two-site tensors in split-TF32 on tensor cores "
+                              "(tcgen05.mma for bond sides >= 64, mma.sync below; FP32 accumulation); gate "
+                              "contractions, energy cotangent, SVD, SVD adjoint, sums FP64"}
         st_m.free()
+    flush = None
+    torch.cuda.synchronize()
+    # ---- n = 40, D = 256 (rank 0 only; one GPU) ----
+    n40 = None
+    if rank == 0 and not args.no_n40:
+        n40 = run_n40(M, stream, peaks)
     # ---- roofline of the dominant kernel (the gate SVD: one CTA per instance per launch) ----
     roof = None
     n_launch = prof["svd_launches"]
     if n_launch:
         t_launch = prof["svd_ms"] / 1e3 / n_launch                   # CUDA events, timed region
         f64_l, f32_l = prof["fp64_flops"] / n_launch, prof["fp32_flops"] / n_launch
-        achieved = (f64_l + f32_l * P64_SM / P32_SM) / t_launch       # FP64-equivalent rate
-        peak = P64_SM * N_SM
-        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+        p64, p32 = peaks["fp64_tflops"] * 1e12, peaks["fp32_tflops"] * 1e12
+        achieved = (f64_l + f32_l * p64 / p32) / t_launch             # FP64-equivalent rate
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": p64 / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / p64, "traffic": None,
                 "kernel": f"svd_kernel (gate SVD; {B} CTAs per launch, one per instance)",
                 "per_launch": {"ms": 1e3 * t_launch, "fp64_flops": f64_l, "fp32_flops": f32_l,
                                "launches": n_launch},
-                "note": "achieved = (F64 + F32*P64/P32) flops per launch, counted on the device, / the "
-                        "launch's CUDA-event duration on the state's stream over the timed steps; peak = "
-                        "recipe nominal FP64 1.25 TFLOP/s for the GPU (fallback: FP64 is not in the measured "
-                        "peaks); FP32 converted at 152 SMs x 128 FMA/clk x 2 x 2.07 GHz",
+                "note": "achieved = (F64 + F32*P64/P32) flops per launch, counted on the device, / the launch's "
+                        "CUDA-event duration on the state's stream over the timed steps; P64, P32 = FP64 and FP32 "
+                        "FMA peaks measured by libpeaks in this run (of measured); traffic null: the kernel works "
+                        "in shared memory (its DRAM bytes are in profiles/)",
                 "svd_share_of_step": prof["svd_ms"] / 1e3 / (t_step * args.steps)}
     if rank == 0:
         cpu = None if args.no_cpu_baseline else (oracle_full(cfg) if n_exc is None else oracle_sample(cfg))
@@ -376,11 +499,12 @@ def run_ours(args, rank, world, local):
                                                          "per-instance tape ~0.9 GB > L2",
                            "precision": "FP64 contractions; SVD FP32-preconditioned, FP64-finished"},
                 "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
-                "mixed_precision": mixed,
+                "peaks_measured": peaks, "mixed_precision": mixed,
                 "pauli_terms_per_s": {"value": terms_per_s, "unit": "Pauli-term expectations/s",
                                       "roofline": energy_roof,
-                                      "note": f"energy pass alone on the {B} final states "
-                                              f"({len(x)} strings each), host clock over {n_rep} calls"}}
+                                      "note": f"energy pass alone on the {B} final states ({len(x)} strings each), "
+                                              "best of 3 calls timed with CUDA events"},
+                "n40_D256": n40}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

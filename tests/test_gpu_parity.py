@@ -644,3 +644,95 @@ def test_config4_prefix_against_oracle_values(M):
     M.apply_circuit(st2, circ, th)
     dims, _, _ = st2.read()
     assert list(dims[1:-1]) == gold["bond_dims"] and max(dims) == 256
+
+
+def test_ill_conditioned_instances_within_the_oracles_own_rounding_spread(M):
+    """Config 1 at the angles of instances 107 and 144 of the bench batch.  Instance 107 keeps
+    Schmidt values down to 5e-11 s_1, including an exactly degenerate pair there, and its FP64
+    gradient is determined only to ~1e-7 by the arithmetic itself: the oracle moves by 7e-8 when
+    LAPACK's other SVD driver (gesvd for gesdd) computes the same SVDs.  The GPU must agree with
+    the oracle within 1e-9 relative or within three times that spread, whichever is larger."""
+    import scipy.linalg as sla
+    p = S.make_problem(1)
+    n_theta = len(p.excitations)
+    insts = (107, 144)
+    th = np.stack([S.random_theta(S.seed_for(1, 500 + i), n_theta) for i in insts])
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    circ = M.Circuit(p.n, M.compile_excitations(p.n, p.excitations))
+    ham = M.Hamiltonian(p.n, x, z, c)
+    st = M.State.product_batch(np.stack([p.bits] * len(insts)), p.spec.D, p.spec.eps)
+    E, g = M.energy_grad(st, circ, th, ham)
+    og = ansatz.compile_circuit(p.n, p.excitations)
+    oh = pauli.jw_hamiltonian(p.h, p.eri)
+    for r in range(len(insts)):
+        ref = OM.energy_grad(OM.init_product(p.bits), og, th[r], oh, p.spec.D, p.spec.eps)
+        orig = np.linalg.svd
+        np.linalg.svd = lambda a, full_matrices=True, compute_uv=True: sla.svd(
+            a, full_matrices=full_matrices, compute_uv=compute_uv, lapack_driver="gesvd")
+        try:
+            alt = OM.energy_grad(OM.init_product(p.bits), og, th[r], oh, p.spec.D, p.spec.eps)
+        finally:
+            np.linalg.svd = orig
+        n0 = np.linalg.norm(ref.grad)
+        spread = np.linalg.norm(alt.grad - ref.grad) / n0
+        assert abs(E[r] - ref.E) <= E_TOL * max(1.0, abs(ref.E))
+        err = np.linalg.norm(g[r] - ref.grad) / n0
+        assert err <= max(G_TOL, 3.0 * spread), (insts[r], err, spread)
+
+
+def test_config2_doubles_against_oracle_values_and_32_central_differences(M):
+    """The differentiation workload (n = 20, D = 128, eps = 1e-10) on sixteen wide singles and six
+    doubles (985 gates): bonds 10-12 reach D = 128 and truncation acts; the reverse pass runs two
+    checkpoint segments of 512 gates.  E and dE/dtheta against the oracle's stored values
+    (tests/golden/make_config2_doubles.py), then central differences (h = 1e-5) on 32 angles
+    evaluated as 64 instances of batched states, against the reverse pass.  A component whose
+    kept bond dimensions differ between theta +- h straddles a change of the truncation (the
+    derivative is one-sided there) and is not compared; at most four may be skipped."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config2_doubles.json")
+    if not os.path.exists(path):
+        pytest.skip("tests/golden/config2_doubles.json not generated (tests/golden/make_config2_doubles.py)")
+    with open(path) as f:
+        gold = json.load(f)
+    p = S.make_problem(2)
+    excs = [p.excitations[t] for t in gold["subset"]]
+    th = np.array([p.theta[t] for t in gold["subset"]])
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    gates = M.compile_excitations(p.n, excs)
+    assert len(gates) == gold["n_gates"] > 512
+    circ = M.Circuit(p.n, gates)
+    ham = M.Hamiltonian(p.n, x, z, c)
+    st = M.State.product(p.bits, p.spec.D, p.spec.eps, checkpoint_every=512)
+    E, g, gg = M.energy_grad(st, circ, th, ham, gate_grad=True)
+    g_ref = np.array(gold["grad"])
+    assert abs(E - gold["E"]) <= E_TOL * max(1.0, abs(gold["E"]))
+    assert np.linalg.norm(g - g_ref) <= G_TOL * max(1.0, np.linalg.norm(g_ref))
+    st1 = M.State.product(p.bits, p.spec.D, p.spec.eps)
+    M.apply_circuit(st1, circ, th)
+    dims, _, _ = st1.read()
+    assert list(dims[1:-1]) == gold["bond_dims"] and max(dims) == 128
+    # 32 central differences, 2 x 32 instances
+    rng = np.random.default_rng(20)
+    comps = rng.choice(len(th), size=min(32, len(th)), replace=len(th) < 32)
+    h = 1e-5
+    fd, ok = [], []
+    for chunk in (comps[:16], comps[16:]):
+        rows = []
+        for j in chunk:
+            for sgn in (1.0, -1.0):
+                t = th.copy()
+                t[j] += sgn * h
+                rows.append(t)
+        stb = M.State.product_batch(np.stack([p.bits] * len(rows)), p.spec.D, p.spec.eps)
+        M.apply_circuit(stb, circ, np.stack(rows))
+        Eb = M.energy(stb, ham)
+        for q in range(len(chunk)):
+            dp, _, _ = stb.read(2 * q)
+            dm, _, _ = stb.read(2 * q + 1)
+            ok.append(np.array_equal(dp, dm))
+            fd.append((Eb[2 * q] - Eb[2 * q + 1]) / (2 * h))
+        stb.free()
+    fd, ok = np.array(fd), np.array(ok)
+    assert ok.sum() >= len(comps) - 4
+    assert np.abs(fd[ok] - g[comps][ok]).max() <= 1e-7 * max(1.0, np.abs(g).max())
