@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     ap.add_argument("--no-n40", action="store_true", help="skip the n = 40, D = 256 measurements")
+    ap.add_argument("--profile-case", default=None,
+                    choices=["zgemm_tc", "zgemm_mma_sync", "zgemm_fp64", "svd_coop"],
+                    help="run one kernel on a synthetic case (two warm-up calls, one timed) for a profiler "
+                         "capture, instead of the benchmark")
+    ap.add_argument("--size", type=int, default=2048, help="matrix side of --profile-case")
     return ap.parse_args()
 
 
@@ -511,9 +516,44 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """One kernel on a seeded synthetic case: a complex n x n x n GEMM through one contraction
+    kernel, or the cooperative SVD of one n x n complex matrix (n <= 512)."""
+    import torch
+    import paper_2211_07983_gb300 as M
+    from paper_2211_07983_gb300 import build
+    build.build()
+    rng = np.random.default_rng(1)
+    n = args.size
+    if args.profile_case == "svd_coop":
+        n = min(n, 512)
+        A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        for _ in range(2):
+            M.svd(A, n // 2, 1e-10)
+        t0 = time.perf_counter()
+        s, V, W, k = M.svd(A, n // 2, 1e-10)
+        dt = time.perf_counter() - t0
+        print(json.dumps({"case": "svd_coop", "n": n, "k": k, "s_wall": dt, "note": "wall clock of mps_svd_dev, "
+                          "host transposes included"}))
+        return
+    eng = {"zgemm_tc": "tcgen05", "zgemm_mma_sync": "mma_sync", "zgemm_fp64": "fp64"}[args.profile_case]
+    A = torch.tensor(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)), device="cuda")
+    B = torch.tensor(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)), device="cuda")
+    for _ in range(2):
+        M.api.zgemm(A, B, "N", "N", eng)
+    torch.cuda.synchronize()
+    t = event_time(torch.cuda.current_stream(), lambda: M.api.zgemm(A, B, "N", "N", eng))
+    print(json.dumps({"case": args.profile_case, "n": n, "s": t, "complex_tflops": 8.0 * n ** 3 / t / 1e12,
+                      "note": "CUDA events around mps_zgemm_mixed_dev (descriptor upload and a synchronise "
+                              "included)"}))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

@@ -153,9 +153,13 @@ struct Cplx<float> {
 };
 
 // Cyclic (round-robin) sweeps over the K columns of X (R rows, column j at X + j*R) with the
-// rotations accumulated into Q (K x K, column j at Q + j*K).  One warp per column pair.  Column
-// norms are recomputed at the start of every sweep and updated by each rotation
-// (alpha' = alpha - t g, beta' = beta + t g), so a pair costs one inner product.
+// rotations accumulated into Q (K x K, column j at Q + j*K).  A column pair is handled by a group
+// of 8 lanes, so one warp works on 4 pairs of a round at once: each lane strides over the rows by
+// 8, the inner product is reduced over the group in three shuffles, and the four pairs' memory
+// accesses and reductions overlap (instruction-level parallelism across pairs, which hides the
+// shared-memory and shuffle latencies that a warp-per-pair ordering exposes).  Column norms are
+// recomputed at the start of every sweep and updated by each rotation (alpha' = alpha - t g,
+// beta' = beta + t g), so a pair costs one inner product.
 //
 // A pair (p, q) with inner product gamma is rotated when |gamma|^2 > tol^2 alpha beta.  The
 // rotation's tangent t = sign(zeta)/(|zeta| + sqrt(1 + zeta^2)), zeta = (beta - alpha)/(2|gamma|),
@@ -170,16 +174,26 @@ struct Cplx<float> {
 // leaves inner products of order K (10 tol)^2, far below tol, so the confirming sweep would
 // rotate nothing.  (A looser bound, early = tol/(2K), was measured to cost 1e-9 in energies.)
 // Returns the number of sweeps run; *converged = 1 when a stopping rule was met.
+constexpr int JG = 8;   // lanes per column pair
+
+template <class T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = JG / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 template <class T>
 __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int R, int K, T tol, T tiny,
                              int max_sweeps, int* flag_sh, int* converged, T* nrm, double* flops,
                              double early, unsigned long long* maxrel_sh) {
   using C2 = typename Cplx<T>::t;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const int grp = lane / JG, gl = lane % JG, per_warp = 32 / JG;
   const int Kp = K + (K & 1);
   const T tol2 = tol * tol;
   int sweep = 0;
-  long long checks = 0, rots = 0;   // per warp (lane 0's count is used)
+  long long checks = 0, rots = 0;   // per group (its first lane's count is used)
   *converged = 0;
   for (; sweep < max_sweeps; ++sweep) {
     for (int j = warp; j < K; j += nwarp) {
@@ -196,31 +210,42 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
       *maxrel_sh = 0ull;
     }
     __syncthreads();
-    double maxrel = 0.0;   // this warp's largest rotated |gamma|^2/(alpha beta) in this sweep
+    double maxrel = 0.0;   // this group's largest rotated |gamma|^2/(alpha beta) in this sweep
     for (int r = 0; r < Kp - 1; ++r) {
-      for (int t = warp; t < Kp / 2; t += nwarp) {
-        int pc, qc;
-        if (t == 0) {
-          pc = r;
-          qc = Kp - 1;
-        } else {
-          pc = (r + t) % (Kp - 1);
-          qc = (r - t + Kp - 1) % (Kp - 1);
+      for (int t0 = warp * per_warp; t0 < Kp / 2; t0 += nwarp * per_warp) {   // uniform over the warp
+        const int t = t0 + grp;
+        int pc = 0, qc = 0;
+        bool live = t < Kp / 2;
+        if (live) {
+          if (t == 0) {
+            pc = r;
+            qc = Kp - 1;
+          } else {
+            pc = (r + t) % (Kp - 1);
+            qc = (r - t + Kp - 1) % (Kp - 1);
+          }
+          live = pc < K && qc < K;
         }
-        if (pc >= K || qc >= K) continue;
-        const T al = nrm[pc], be = nrm[qc];
-        if (al < tiny || be < tiny) continue;
+        T al = 0, be = 0;
+        if (live) {
+          al = nrm[pc];
+          be = nrm[qc];
+          live = !(al < tiny || be < tiny);
+        }
         C2* ap = X + (size_t)pc * R;
         C2* aq = X + (size_t)qc * R;
-        ++checks;
         T gr = 0, gi = 0;
-        for (int i = lane; i < R; i += 32) {
-          const C2 x = ap[i], y = aq[i];
-          gr += x.x * y.x + x.y * y.y;   // conj(x) y
-          gi += x.x * y.y - x.y * y.x;
+        if (live) {
+          for (int i = gl; i < R; i += JG) {
+            const C2 x = ap[i], y = aq[i];
+            gr += x.x * y.x + x.y * y.y;   // conj(x) y
+            gi += x.x * y.y - x.y * y.x;
+          }
         }
-        gr = Cplx<T>::sum(gr);
-        gi = Cplx<T>::sum(gi);
+        gr = group_sum(gr);   // every lane of the warp takes part in the shuffles
+        gi = group_sum(gi);
+        if (!live) continue;
+        if (gl == 0) ++checks;
         const T g2 = gr * gr + gi * gi;
         const T ab = al * be;
         if (!(g2 > tol2 * ab)) continue;
@@ -235,20 +260,20 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
         maxrel = fmax(maxrel, (double)(g2 / ab));
         // a_p' = c a_p - s e^{-i phi} a_q ; a_q' = s e^{i phi} a_p + c a_q
         const T spr = s * pr, spi = s * pim;
-        for (int i = lane; i < R; i += 32) {
+        for (int i = gl; i < R; i += JG) {
           const C2 x = ap[i], y = aq[i];
           ap[i] = Cplx<T>::mk(c * x.x - (spr * y.x + spi * y.y), c * x.y - (spr * y.y - spi * y.x));
           aq[i] = Cplx<T>::mk(spr * x.x - spi * x.y + c * y.x, spr * x.y + spi * x.x + c * y.y);
         }
         C2* vp = Q + (size_t)pc * K;
         C2* vq = Q + (size_t)qc * K;
-        for (int i = lane; i < K; i += 32) {
+        for (int i = gl; i < K; i += JG) {
           const C2 x = vp[i], y = vq[i];
           vp[i] = Cplx<T>::mk(c * x.x - (spr * y.x + spi * y.y), c * x.y - (spr * y.y - spi * y.x));
           vq[i] = Cplx<T>::mk(spr * x.x - spi * x.y + c * y.x, spr * x.y + spi * x.x + c * y.y);
         }
-        ++rots;
-        if (lane == 0) {
+        if (gl == 0) {
+          ++rots;
           nrm[pc] = al - tt * g;
           nrm[qc] = be + tt * g;
           *flag_sh = 1;
@@ -257,7 +282,7 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
       __syncthreads();
     }
     // largest rotation of the sweep (non-negative doubles order like their bit patterns)
-    if (lane == 0 && maxrel > 0.0) atomicMax(maxrel_sh, (unsigned long long)__double_as_longlong(maxrel));
+    if (gl == 0 && maxrel > 0.0) atomicMax(maxrel_sh, (unsigned long long)__double_as_longlong(maxrel));
     __syncthreads();
     const int rot = *flag_sh;
     const double mr = __longlong_as_double((long long)*maxrel_sh);
@@ -270,11 +295,11 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
   }
   // work actually done: per sweep K column norms (4R flops each), per checked pair one complex
   // inner product (8R), per rotation the update of two columns of X (24R) and of Q (24K)
-  if (flops && lane == 0) {
-    double f = 8.0 * R * (double)checks + (24.0 * R + 24.0 * K) * (double)rots;
-    if (warp == 0) f += 4.0 * R * K * (double)sweep;
+  if (flops && gl == 0 && (checks | rots)) {
+    const double f = 8.0 * R * (double)checks + (24.0 * R + 24.0 * K) * (double)rots;
     atomicAdd(flops, f);
   }
+  if (flops && tid == 0) atomicAdd(flops, 4.0 * R * K * (double)sweep);
   return sweep;
 }
 

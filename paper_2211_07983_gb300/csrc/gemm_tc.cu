@@ -55,13 +55,56 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   return r;
 }
 
-__device__ __forceinline__ double2 ld_op(const double2* X, int ld, int op, int r, int c) {
-  switch (op) {   // element (r, c) of op(X)
-    case OP_N: return X[(size_t)r * ld + c];
-    case OP_T: return X[(size_t)c * ld + r];
-    case OP_H: return conjd(X[(size_t)c * ld + r]);
-    default: return conjd(X[(size_t)r * ld + c]);
-  }
+// Element (r, c) of op(X) without the conjugation (applied after the conversion to FP32).
+__device__ __forceinline__ double2 ld_raw(const double2* X, int ld, int op, int r, int c) {
+  return (op == OP_N || op == OP_C) ? X[(size_t)r * ld + c] : X[(size_t)c * ld + r];
+}
+
+// FP64 -> FP32 (round to nearest even) in integer arithmetic.  GB300 runs FP64 instructions,
+// conversions included, at 1/64 of the FP32 rate, and every operand element passes through here;
+// the integer pipe does it at full rate.  Values below the FP32 normal range become (signed) zero:
+// a GEMM operand that small is below the split-TF32 resolution of any product it enters.
+__device__ __forceinline__ uint32_t f64_to_f32_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FF);
+  const uint32_t mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const uint32_t rem = lo & 0x1FFFFFFFu;
+  if (e == 0x7FF) return sign | 0x7F800000u | ((mant | rem) ? 0x400000u : 0u);
+  const int ef = e - 896;   // rebias 1023 -> 127
+  if (ef >= 255) return sign | 0x7F800000u;
+  if (ef <= 0) return sign;
+  uint32_t f = sign | ((uint32_t)ef << 23) | mant;
+  // a carry out of the mantissa moves into the exponent: still the correctly rounded result
+  if (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) f += 1u;
+  return f;
+}
+
+// FP32 -> FP64 (exact) in integer arithmetic; denormal inputs take the hardware conversion.
+__device__ __forceinline__ double f32_to_f64(float v) {
+  const uint32_t f = __float_as_uint(v);
+  const uint32_t e = (f >> 23) & 0xFFu, m = f & 0x7FFFFFu, sign = f & 0x80000000u;
+  if (e == 0u) return m == 0u ? __longlong_as_double((long long)((unsigned long long)sign << 32)) : (double)v;
+  const uint32_t eh = e == 0xFFu ? 0x7FFu : e + 896u;
+  const unsigned long long d =
+      ((unsigned long long)(sign | (eh << 20) | (m >> 3)) << 32) | ((unsigned long long)(m & 7u) << 29);
+  return __longlong_as_double((long long)d);
+}
+
+// hi/lo TF32 parts of the real and imaginary part of a complex FP64 operand element
+struct Split4 {
+  uint32_t rh, rl, ih, il;
+};
+__device__ __forceinline__ Split4 split_c(double2 v, bool conj) {
+  const float fr = __uint_as_float(f64_to_f32_bits(v.x));
+  const float fi = __uint_as_float(f64_to_f32_bits(v.y) ^ (conj ? 0x80000000u : 0u));
+  Split4 o;
+  o.rh = to_tf32(fr);
+  o.ih = to_tf32(fi);
+  o.rl = to_tf32(fr - __uint_as_float(o.rh));
+  o.il = to_tf32(fi - __uint_as_float(o.ih));
+  return o;
 }
 
 // byte offset of element (row, k) of a 128 x 16 K-major operand part in the canonical
@@ -150,31 +193,33 @@ __device__ void tc_tile(const GemmDesc& d0, int row0, int col0, size_t io, int* 
     }
     const int k0 = c * TC_KC;
     // A: 128 x 16 elements of op(A), B: 16 x 128 elements of op(B) stored as 128 (n) x 16 (k)
+    // Consecutive threads take consecutive addresses of the operand in memory: along k when the
+    // operand's rows are contiguous in k (op N, C), along the row index otherwise (op T, H).
+    const bool a_kfast = (d.opA == OP_N || d.opA == OP_C), b_kfast = !(d.opB == OP_N || d.opB == OP_C);
+    const bool a_conj = (d.opA == OP_H || d.opA == OP_C), b_conj = (d.opB == OP_H || d.opB == OP_C);
+#pragma unroll 4
     for (int e = tid; e < TC_M * TC_KC; e += TC_THREADS) {
-      const int r = e / TC_KC, k = e % TC_KC;
+      const int r = a_kfast ? e / TC_KC : e % TC_M, k = a_kfast ? e % TC_KC : e / TC_M;
       const int gr = row0 + r, gk = k0 + k;
-      const double2 v = (gr < M && gk < K) ? ld_op(d.A, lda, d.opA, gr, gk) : make_double2(0.0, 0.0);
-      const float fr = (float)v.x, fi = (float)v.y;
-      const uint32_t hr = to_tf32(fr), hi_ = to_tf32(fi);
-      const uint32_t lr = to_tf32(fr - __uint_as_float(hr)), li = to_tf32(fi - __uint_as_float(hi_));
+      const double2 v = (gr < M && gk < K) ? ld_raw(d.A, lda, d.opA, gr, gk) : make_double2(0.0, 0.0);
+      const Split4 q = split_c(v, a_conj);
       const uint32_t o = kmajor_off(r, k);
-      *reinterpret_cast<uint32_t*>(sp + 0 * TC_PART + o) = hr;
-      *reinterpret_cast<uint32_t*>(sp + 1 * TC_PART + o) = lr;
-      *reinterpret_cast<uint32_t*>(sp + 2 * TC_PART + o) = hi_;
-      *reinterpret_cast<uint32_t*>(sp + 3 * TC_PART + o) = li;
+      *reinterpret_cast<uint32_t*>(sp + 0 * TC_PART + o) = q.rh;
+      *reinterpret_cast<uint32_t*>(sp + 1 * TC_PART + o) = q.rl;
+      *reinterpret_cast<uint32_t*>(sp + 2 * TC_PART + o) = q.ih;
+      *reinterpret_cast<uint32_t*>(sp + 3 * TC_PART + o) = q.il;
     }
+#pragma unroll 4
     for (int e = tid; e < TC_N * TC_KC; e += TC_THREADS) {
-      const int nn = e % TC_N, k = e / TC_N;   // consecutive threads: consecutive columns of op(B)
+      const int nn = b_kfast ? e / TC_KC : e % TC_N, k = b_kfast ? e % TC_KC : e / TC_N;
       const int gn = col0 + nn, gk = k0 + k;
-      const double2 v = (gn < N && gk < K) ? ld_op(d.B, ldb, d.opB, gk, gn) : make_double2(0.0, 0.0);
-      const float fr = (float)v.x, fi = (float)v.y;
-      const uint32_t hr = to_tf32(fr), hi_ = to_tf32(fi);
-      const uint32_t lr = to_tf32(fr - __uint_as_float(hr)), li = to_tf32(fi - __uint_as_float(hi_));
+      const double2 v = (gn < N && gk < K) ? ld_raw(d.B, ldb, d.opB, gk, gn) : make_double2(0.0, 0.0);
+      const Split4 q = split_c(v, b_conj);
       const uint32_t o = kmajor_off(nn, k);
-      *reinterpret_cast<uint32_t*>(sp + 4 * TC_PART + o) = hr;
-      *reinterpret_cast<uint32_t*>(sp + 5 * TC_PART + o) = lr;
-      *reinterpret_cast<uint32_t*>(sp + 6 * TC_PART + o) = hi_;
-      *reinterpret_cast<uint32_t*>(sp + 7 * TC_PART + o) = li;
+      *reinterpret_cast<uint32_t*>(sp + 4 * TC_PART + o) = q.rh;
+      *reinterpret_cast<uint32_t*>(sp + 5 * TC_PART + o) = q.rl;
+      *reinterpret_cast<uint32_t*>(sp + 6 * TC_PART + o) = q.ih;
+      *reinterpret_cast<uint32_t*>(sp + 7 * TC_PART + o) = q.il;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic stores -> tensor-core reads
     __syncthreads();
@@ -224,6 +269,7 @@ __device__ void tc_tile(const GemmDesc& d0, int row0, int col0, size_t io, int* 
   // epilogue: warp w owns accumulator rows (TMEM lanes) 32w .. 32w + 31
   const int r = row0 + warp * 32 + lane;
   const bool zero_beta = (d.beta.x == 0.0 && d.beta.y == 0.0);
+  const bool unit_alpha = (d.alpha.x == 1.0 && d.alpha.y == 0.0);
   const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
   for (int cb = 0; cb < TC_N; cb += 16) {
@@ -235,8 +281,9 @@ __device__ void tc_tile(const GemmDesc& d0, int row0, int col0, size_t io, int* 
       for (int j = 0; j < 16; ++j) {
         const int cc = col0 + cb + j;
         if (cc >= N) break;
-        double2 v = cmul(d.alpha, make_double2((double)vr[j], (double)vi[j]));
+        double2 v = make_double2(f32_to_f64(vr[j]), f32_to_f64(vi[j]));
         double2* out = d.C + (size_t)r * ldc + cc;
+        if (!unit_alpha) v = cmul(d.alpha, v);
         if (!zero_beta) v = cadd(v, cmul(d.beta, *out));
         *out = v;
       }
