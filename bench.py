@@ -55,8 +55,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     ap.add_argument("--no-n40", action="store_true", help="skip the n = 40, D = 256 measurements")
+    ap.add_argument("--no-psr", action="store_true", help="skip the parameter-shift comparison")
     ap.add_argument("--profile-case", default=None,
-                    choices=["zgemm_tc", "zgemm_mma_sync", "zgemm_fp64", "svd_coop"],
+                    choices=["zgemm_tc", "zgemm_mma_sync", "zgemm_fp64", "svd_coop", "step"],
                     help="run one kernel on a synthetic case (two warm-up calls, one timed) for a profiler "
                          "capture, instead of the benchmark")
     ap.add_argument("--size", type=int, default=2048, help="matrix side of --profile-case")
@@ -336,6 +337,39 @@ def run_n40(M, stream, peaks):
     return out
 
 
+def run_psr(M, stream):
+    """Parameter shift (2 M shifted circuits as batched instances) against one adjoint evaluation,
+    on prefixes of the n = 12 workload: t_PSR / t_grad as M grows (Sec. 4, Eq. psr)."""
+    import torch
+    from paper_2211_07983_gb300 import psr
+    p = S.make_problem(1)
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    ham = M.Hamiltonian(p.n, x, z, c)
+    rows = []
+    for n_exc in (4, 8, 16, 32):
+        excs = p.excitations[:n_exc]
+        gates = M.compile_excitations(p.n, excs)
+        circ = M.Circuit(p.n, gates)
+        th = p.theta[:n_exc]
+        st = M.State.product(p.bits, p.spec.D, p.spec.eps, stream=stream)
+        M.energy_grad(st, circ, th, ham)                       # warm-up (plans)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        E, g = M.energy_grad(st, circ, th, ham)
+        t_grad = time.perf_counter() - t0
+        st.free()
+        gp, _, n_eval, _ = psr.parameter_shift(p.n, p.bits, gates, th, ham, p.spec.D, p.spec.eps, batch=256,
+                                               stream=stream)  # warm-up
+        gp, _, n_eval, t_psr = psr.parameter_shift(p.n, p.bits, gates, th, ham, p.spec.D, p.spec.eps, batch=256,
+                                                   stream=stream)
+        rows.append({"excitations": n_exc, "M_theta": n_exc, "M_rz": n_eval // 2, "gates": len(gates),
+                     "t_grad_s": t_grad, "t_psr_s": t_psr, "ratio": t_psr / t_grad,
+                     "rel_diff": float(np.linalg.norm(gp - g) / max(1e-300, np.linalg.norm(g)))})
+    return {"workload": "prefixes of n12_D64 (no truncation), one instance", "rows": rows,
+            "note": "host wall clock of one mps_energy_grad call against the whole parameter-shift gradient "
+                    "(2 M_rz forward passes and energies, 256 instances per batched state)"}
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2211_07983_gb300 as M
@@ -474,6 +508,9 @@ def run_ours(args, rank, world, local):
     n40 = None
     if rank == 0 and not args.no_n40:
         n40 = run_n40(M, stream, peaks)
+    psr_rows = None
+    if rank == 0 and not args.no_psr:
+        psr_rows = run_psr(M, stream)
     # ---- roofline of the dominant kernel (the gate SVD: one CTA per instance per launch) ----
     roof = None
     n_launch = prof["svd_launches"]
@@ -509,7 +546,7 @@ def run_ours(args, rank, world, local):
                                       "roofline": energy_roof,
                                       "note": f"energy pass alone on the {B} final states ({len(x)} strings each), "
                                               "best of 3 calls timed with CUDA events"},
-                "n40_D256": n40}
+                "n40_D256": n40, "psr": psr_rows}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -525,6 +562,23 @@ def run_profile_case(args):
     build.build()
     rng = np.random.default_rng(1)
     n = args.size
+    if args.profile_case == "step":
+        # one eager energy + gradient evaluation of --workload on --instances instances
+        cfg, n_exc = WORKLOADS[args.workload]
+        p = S.make_problem(cfg)
+        excs = p.excitations if n_exc is None else p.excitations[:n_exc]
+        x, z, c = M.build_hamiltonian(p.h, p.eri)
+        circ = M.Circuit(p.n, M.compile_excitations(p.n, excs))
+        ham = M.Hamiltonian(p.n, x, z, c)
+        B = args.instances
+        th = np.stack([S.random_theta(S.seed_for(1, 500 + i), len(excs)) for i in range(B)])
+        st = M.State.product_batch(np.stack([p.bits] * B), p.spec.D, p.spec.eps)
+        l0 = M.kernel_launches()
+        t0 = time.perf_counter()
+        M.energy_grad(st, circ, th, ham)
+        print(json.dumps({"case": "step", "workload": args.workload, "instances": B, "s_wall": time.perf_counter() - t0,
+                          "launches": M.kernel_launches() - l0}))
+        return
     if args.profile_case == "svd_coop":
         n = min(n, 512)
         A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))

@@ -235,6 +235,29 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
                                double* grad_out, double* gate_grad_out);
 
 /*
+ * E and dE/dtheta with the Pauli strings split over processes (one process per GPU).  E and the
+ * energy cotangent dE/dB* are linear in the strings once divided by the common <psi|psi>
+ * (Sec. 2, Eq. expect-val; Sec. 4, Eq. expecgrad): with H = sum_r H_r, E = sum_r E_r and
+ * dE/dB* = sum_r [env_{H_r} - E_r env_I] / <psi|psi>.  So every rank runs the (replicated) forward
+ * pass, the energy and cotangent of its own strings, one sum-allreduce of (E_r, Bbar_r) by the
+ * caller, then the (replicated) reverse pass from the summed cotangent.  The identity string
+ * belongs to exactly one rank's H_r.
+ *   begin: forward + energy + cotangent of h_shard (its strings only); E_out: one value per
+ *          instance, host or device; Bbar_out: device memory of mps_cotangent_size() doubles
+ *          (instance-major, the state's site slots at the bond caps, interleaved complex).
+ *   end:   reverse pass from Bbar_in (device, the summed cotangent, same layout); grad_out and
+ *          gate_grad_out as in mps_energy_grad_dev.  Requires a begin with the same circuit on
+ *          this state just before it (no other call on the state in between); n_theta as in begin.
+ */
+mps_status mps_energy_grad_shard_begin(const mps_state* s0, const mps_circuit* c, const double* theta,
+                                       int32_t n_theta, const mps_hamiltonian_dev* h_shard, double* E_out,
+                                       double* Bbar_out);
+mps_status mps_energy_grad_shard_end(const mps_state* s0, const mps_circuit* c, int32_t n_theta,
+                                     const double* Bbar_in, double* grad_out, double* gate_grad_out);
+/* Number of doubles of a state's cotangent buffer (all instances). */
+mps_status mps_cotangent_size(const mps_state* s, int64_t* n_doubles);
+
+/*
  * The gate SVD on its own (steps S3-S4, Sec. 3): one-sided Jacobi SVD of a complex m x ncol
  * matrix A (m, ncol even, <= 512) on its shorter side, FP32 preconditioning sweeps followed by
  * FP64 re-orthonormalisation and FP64 sweeps (FP64-accurate result), sorted descending, then

@@ -78,6 +78,10 @@ _SIGS = {
                               c_void_p]),
     "mps_zgemm_mixed_dev": (c_int32, [c_int32, c_int32, c_int32, c_void_p, c_int32, c_int32, c_void_p, c_int32,
                                       c_int32, c_void_p, c_int32, c_int32]),
+    "mps_energy_grad_shard_begin": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p,
+                                              c_void_p]),
+    "mps_energy_grad_shard_end": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
+    "mps_cotangent_size": (c_int32, [c_void_p, P(c_int64)]),
     "mps_profile": (c_int32, [c_void_p, c_int32]),
     "mps_profile_read": (c_int32, [c_void_p, c_void_p]),
     "mps_profile_svd_phases": (c_int32, [c_void_p, c_void_p]),

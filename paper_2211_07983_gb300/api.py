@@ -340,6 +340,37 @@ def energy_grad_host(state0: State, gates, theta, x, z, c, gate_grad=False):
     return (Ev, g, gg) if gate_grad else (Ev, g)
 
 
+def cotangent_size(state: State) -> int:
+    """mps_cotangent_size: doubles of the state's cotangent buffer (all instances)."""
+    n = ctypes.c_int64(0)
+    check(_lib.load().mps_cotangent_size(state._h, ctypes.byref(n)))
+    return int(n.value)
+
+
+def energy_grad_shard_begin(state0: State, circuit: Circuit, theta, ham_shard: Hamiltonian):
+    """mps_energy_grad_shard_begin: forward pass, then E_r and the cotangent of this shard's strings.
+
+    Returns (E_r, Bbar_r) as float64 CUDA tensors ([n_inst] and [cotangent_size]) to be summed
+    over the ranks before energy_grad_shard_end."""
+    import torch
+    theta = _f64(theta)
+    nth = _n_theta(state0, theta)
+    E = torch.zeros(state0.n_inst, dtype=torch.float64, device="cuda")
+    Bbar = torch.zeros(cotangent_size(state0), dtype=torch.float64, device="cuda")
+    check(_lib.load().mps_energy_grad_shard_begin(state0._h, circuit._h, _ptr(theta), nth, ham_shard._h, _ptr(E),
+                                                  _ptr(Bbar)))
+    return E, Bbar
+
+
+def energy_grad_shard_end(state0: State, circuit: Circuit, n_theta: int, Bbar, gate_grad: bool = False):
+    """mps_energy_grad_shard_end: the reverse pass from the summed cotangent -> dE/dtheta."""
+    ni = state0.n_inst
+    g = np.zeros((ni, n_theta) if ni > 1 else n_theta)
+    gg = (np.zeros((ni, circuit.n_gates) if ni > 1 else circuit.n_gates)) if gate_grad else None
+    check(_lib.load().mps_energy_grad_shard_end(state0._h, circuit._h, n_theta, _ptr(Bbar), _ptr(g), _ptr(gg)))
+    return (g, gg) if gate_grad else g
+
+
 def svd(A: np.ndarray, D: int, eps: float):
     """mps_svd_dev: the GPU gate SVD of one complex matrix -> (s, V, W = A V, k)."""
     A = np.ascontiguousarray(A, dtype=np.complex128)

@@ -10,7 +10,7 @@
 // (the minus sign is the instruction descriptor's negate-A bit), so one k-step of 8 issues
 // 4 x 3 = 12 MMAs of 128 x 128 x 8.  The result is accurate to about FP32 rounding.
 //
-// Tile and pipeline.  One CTA of 4 warps computes a 128 x 128 output tile.  K advances in chunks
+// Tile and pipeline.  One CTA of 8 warps computes a 128 x 128 output tile.  K advances in chunks
 // of 16: all threads read the FP64 operands (any op: N, T, H, C), split them and store the hi/lo
 // parts of Re and Im in shared memory in the K-major, no-swizzle canonical layout of the MMA
 // (8-row x 16-byte core matrices, core matrices adjacent in K 128 bytes apart, adjacent in M/N
@@ -31,7 +31,9 @@ namespace mpsk {
 
 namespace {
 
-constexpr int TC_M = 128, TC_N = 128, TC_KC = 16, TC_THREADS = 128, TC_STAGES = 2;
+constexpr int TC_M = 128, TC_N = 128, TC_KC = 16, TC_THREADS = 256, TC_STAGES = 2;
+// operand elements each thread stages per chunk (A and B each)
+constexpr int TC_PER = TC_M * TC_KC / TC_THREADS;
 constexpr int TC_TMEM_COLS = 256;                        // D_re: columns 0..127, D_im: 128..255
 // one operand part (128 rows x 16 tf32) = 8 KB; parts per stage: A {re,im} x {hi,lo}, B likewise
 constexpr int TC_PART = TC_M * TC_KC * 4;
@@ -170,6 +172,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 
 // One 128 x 128 output tile of descriptor d (instance offset io).  Parts of a stage, in order:
 // A re hi, A re lo, A im hi, A im lo, B re hi, B re lo, B im hi, B im lo.
+//
+// Producer: each thread holds TC_PER elements of A and of B for one chunk in registers.  The
+// loads of chunk c+1 are issued right after chunk c is converted into shared memory, so they are
+// in flight while the MMAs of chunk c run and while the next stage waits to be free.
 __device__ void tc_tile(const GemmDesc& d0, int row0, int col0, size_t io, int* status, unsigned char* smem,
                         uint32_t tmem, uint32_t mbar0) {
   GemmDesc d = d0;
@@ -184,6 +190,53 @@ __device__ void tc_tile(const GemmDesc& d0, int row0, int col0, size_t io, int* 
   const uint32_t sbase = smem_u32(smem);
   uint32_t phase[TC_STAGES] = {0u, 0u};
   bool ok = true;
+  // Consecutive threads take consecutive addresses of an operand in memory: along k when its rows
+  // are contiguous in k (op N, C for A; op T, H for B), along the other index otherwise.
+  const bool a_kfast = (d.opA == OP_N || d.opA == OP_C), b_kfast = !(d.opB == OP_N || d.opB == OP_C);
+  const bool a_conj = (d.opA == OP_H || d.opA == OP_C), b_conj = (d.opB == OP_H || d.opB == OP_C);
+  double2 ra[TC_PER], rb[TC_PER];
+  auto load_chunk = [&](int c) {
+    const int k0 = c * TC_KC;
+#pragma unroll
+    for (int i = 0; i < TC_PER; ++i) {
+      const int e = tid + i * TC_THREADS;
+      const int r = a_kfast ? e / TC_KC : e % TC_M, k = a_kfast ? e % TC_KC : e / TC_M;
+      const int gr = row0 + r, gk = k0 + k;
+      ra[i] = (gr < M && gk < K) ? ld_raw(d.A, lda, d.opA, gr, gk) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int i = 0; i < TC_PER; ++i) {
+      const int e = tid + i * TC_THREADS;
+      const int nn = b_kfast ? e / TC_KC : e % TC_N, k = b_kfast ? e % TC_KC : e / TC_N;
+      const int gn = col0 + nn, gk = k0 + k;
+      rb[i] = (gn < N && gk < K) ? ld_raw(d.B, ldb, d.opB, gk, gn) : make_double2(0.0, 0.0);
+    }
+  };
+  auto store_chunk = [&](unsigned char* sp) {
+#pragma unroll
+    for (int i = 0; i < TC_PER; ++i) {
+      const int e = tid + i * TC_THREADS;
+      const int r = a_kfast ? e / TC_KC : e % TC_M, k = a_kfast ? e % TC_KC : e / TC_M;
+      const Split4 q = split_c(ra[i], a_conj);
+      const uint32_t o = kmajor_off(r, k);
+      *reinterpret_cast<uint32_t*>(sp + 0 * TC_PART + o) = q.rh;
+      *reinterpret_cast<uint32_t*>(sp + 1 * TC_PART + o) = q.rl;
+      *reinterpret_cast<uint32_t*>(sp + 2 * TC_PART + o) = q.ih;
+      *reinterpret_cast<uint32_t*>(sp + 3 * TC_PART + o) = q.il;
+    }
+#pragma unroll
+    for (int i = 0; i < TC_PER; ++i) {
+      const int e = tid + i * TC_THREADS;
+      const int nn = b_kfast ? e / TC_KC : e % TC_N, k = b_kfast ? e % TC_KC : e / TC_N;
+      const Split4 q = split_c(rb[i], b_conj);
+      const uint32_t o = kmajor_off(nn, k);
+      *reinterpret_cast<uint32_t*>(sp + 4 * TC_PART + o) = q.rh;
+      *reinterpret_cast<uint32_t*>(sp + 5 * TC_PART + o) = q.rl;
+      *reinterpret_cast<uint32_t*>(sp + 6 * TC_PART + o) = q.ih;
+      *reinterpret_cast<uint32_t*>(sp + 7 * TC_PART + o) = q.il;
+    }
+  };
+  if (nchunks > 0) load_chunk(0);
   for (int c = 0; c < nchunks; ++c) {
     const int st = c % TC_STAGES;
     unsigned char* sp = smem + st * TC_STAGE_BYTES;
@@ -191,36 +244,8 @@ __device__ void tc_tile(const GemmDesc& d0, int row0, int col0, size_t io, int* 
       if (!mbar_wait(mbar0 + 8 * st, phase[st])) ok = false;
       phase[st] ^= 1u;
     }
-    const int k0 = c * TC_KC;
-    // A: 128 x 16 elements of op(A), B: 16 x 128 elements of op(B) stored as 128 (n) x 16 (k)
-    // Consecutive threads take consecutive addresses of the operand in memory: along k when the
-    // operand's rows are contiguous in k (op N, C), along the row index otherwise (op T, H).
-    const bool a_kfast = (d.opA == OP_N || d.opA == OP_C), b_kfast = !(d.opB == OP_N || d.opB == OP_C);
-    const bool a_conj = (d.opA == OP_H || d.opA == OP_C), b_conj = (d.opB == OP_H || d.opB == OP_C);
-#pragma unroll 4
-    for (int e = tid; e < TC_M * TC_KC; e += TC_THREADS) {
-      const int r = a_kfast ? e / TC_KC : e % TC_M, k = a_kfast ? e % TC_KC : e / TC_M;
-      const int gr = row0 + r, gk = k0 + k;
-      const double2 v = (gr < M && gk < K) ? ld_raw(d.A, lda, d.opA, gr, gk) : make_double2(0.0, 0.0);
-      const Split4 q = split_c(v, a_conj);
-      const uint32_t o = kmajor_off(r, k);
-      *reinterpret_cast<uint32_t*>(sp + 0 * TC_PART + o) = q.rh;
-      *reinterpret_cast<uint32_t*>(sp + 1 * TC_PART + o) = q.rl;
-      *reinterpret_cast<uint32_t*>(sp + 2 * TC_PART + o) = q.ih;
-      *reinterpret_cast<uint32_t*>(sp + 3 * TC_PART + o) = q.il;
-    }
-#pragma unroll 4
-    for (int e = tid; e < TC_N * TC_KC; e += TC_THREADS) {
-      const int nn = b_kfast ? e / TC_KC : e % TC_N, k = b_kfast ? e % TC_KC : e / TC_N;
-      const int gn = col0 + nn, gk = k0 + k;
-      const double2 v = (gn < N && gk < K) ? ld_raw(d.B, ldb, d.opB, gk, gn) : make_double2(0.0, 0.0);
-      const Split4 q = split_c(v, b_conj);
-      const uint32_t o = kmajor_off(nn, k);
-      *reinterpret_cast<uint32_t*>(sp + 4 * TC_PART + o) = q.rh;
-      *reinterpret_cast<uint32_t*>(sp + 5 * TC_PART + o) = q.rl;
-      *reinterpret_cast<uint32_t*>(sp + 6 * TC_PART + o) = q.ih;
-      *reinterpret_cast<uint32_t*>(sp + 7 * TC_PART + o) = q.il;
-    }
+    store_chunk(sp);
+    if (c + 1 < nchunks) load_chunk(c + 1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic stores -> tensor-core reads
     __syncthreads();
     if (tid == 0) {
@@ -253,11 +278,9 @@ __device__ void tc_tile(const GemmDesc& d0, int row0, int col0, size_t io, int* 
       }
       mma_commit(mbar0 + 8 * st);
     }
-    __syncthreads();
   }
   // wait for the last commit of each stage that was used
   for (int st = 0; st < TC_STAGES && st < nchunks; ++st) {
-    // the last chunk that used stage st
     if (!mbar_wait(mbar0 + 8 * st, phase[st])) ok = false;
     phase[st] ^= 1u;
   }
@@ -266,13 +289,15 @@ __device__ void tc_tile(const GemmDesc& d0, int row0, int col0, size_t io, int* 
     if (tid == 0) set_status(status, MPS_ETIMEOUT);
     return;
   }
-  // epilogue: warp w owns accumulator rows (TMEM lanes) 32w .. 32w + 31
-  const int r = row0 + warp * 32 + lane;
+  // epilogue: warp w reads accumulator rows (TMEM lanes) 32 (w % 4) .. + 31 and the column half
+  // w / 4 of each accumulator
+  const int q4 = warp & 3, half = warp >> 2;
+  const int r = row0 + q4 * 32 + lane;
   const bool zero_beta = (d.beta.x == 0.0 && d.beta.y == 0.0);
   const bool unit_alpha = (d.alpha.x == 1.0 && d.alpha.y == 0.0);
-  const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16);
 #pragma unroll 1
-  for (int cb = 0; cb < TC_N; cb += 16) {
+  for (int cb = half * (TC_N / 2); cb < (half + 1) * (TC_N / 2); cb += 16) {
     float vr[16], vi[16];
     tmem_ld16(lane_base + cb, vr);
     tmem_ld16(lane_base + TC_N + cb, vi);

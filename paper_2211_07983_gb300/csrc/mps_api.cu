@@ -195,6 +195,7 @@ struct Workspace {
   };
   std::vector<Pending> pending;   // host outputs to copy out of the staging after the call
   cudaEvent_t done = nullptr;     // blocking-sync event: waiting threads sleep instead of spinning
+  long long shard_uid = -1;       // circuit of a pending mps_energy_grad_shard_begin
   long long auto_uid = -1;        // circuit for which the automatic checkpoint interval was chosen
   int auto_K = 0;
   // Host-argument calls (mps_apply_circuit, mps_energy, mps_energy_grad) upload their gate list
@@ -1640,20 +1641,42 @@ mps_status mps_energy(const mps_state* s, const mps_hamiltonian* h, double* E_ou
   return mps_energy_dev(s, hd, E_out, nullptr);
 }
 
-mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const double* theta, int32_t n_theta,
-                               const mps_hamiltonian_dev* hc, double* E_out, double* grad_out,
-                               double* gate_grad_out) {
-  clear_error();
-  if (!s0 || !hc || !E_out || (n_theta > 0 && !grad_out)) return fail(MPS_EINVAL, "mps_energy_grad: NULL argument");
+}  // extern "C"
+
+namespace mpsi {
+
+// The energy + gradient evaluation, whole (RUN_FULL) or in the two halves of a string-sharded
+// evaluation: RUN_BEGIN = forward pass, energy and cotangent of this rank's strings (the
+// cotangent copied to Bbar_io); RUN_END = the reverse pass from the cotangent in Bbar_io (summed
+// over the ranks by the caller).  Between the halves the workspace keeps the forward's snapshots
+// or tape and the gate matrices.
+enum RunMode { RUN_FULL = 0, RUN_BEGIN = 1, RUN_END = 2 };
+
+static mps_status energy_grad_run(int mode, const mps_state* s0, const mps_circuit* c, const double* theta,
+                                  int32_t n_theta, const mps_hamiltonian_dev* hc, double* E_out, double* grad_out,
+                                  double* gate_grad_out, double* Bbar_io) {
+  const char* where = mode == RUN_FULL ? "mps_energy_grad" : mode == RUN_BEGIN ? "mps_energy_grad_shard_begin"
+                                                                               : "mps_energy_grad_shard_end";
+  if (!s0) return fail(MPS_EINVAL, std::string(where) + ": state is NULL");
+  if (mode != RUN_END && (!hc || !E_out)) return fail(MPS_EINVAL, std::string(where) + ": NULL argument");
+  if (mode != RUN_BEGIN && n_theta > 0 && !grad_out) return fail(MPS_EINVAL, std::string(where) + ": grad_out is NULL");
   mps_state* s = const_cast<mps_state*>(s0);
   mps_hamiltonian_dev* h = const_cast<mps_hamiltonian_dev*>(hc);
-  if (h->n != s->L.n) return fail(MPS_EINVAL, "mps_energy_grad: Hamiltonian and state have different qubit counts");
+  if (h && h->n != s->L.n) return fail(MPS_EINVAL, std::string(where) + ": Hamiltonian and state have different qubit counts");
   MPS_TRY(check_circuit(s, c, n_theta));
   const Layout& L = s->L;
   Workspace& w = *s->ws;
+  const size_t bbar_doubles = 2 * L.site_elems();
+  if (mode != RUN_FULL) {
+    if (!Bbar_io) return fail(MPS_EINVAL, std::string(where) + ": Bbar is NULL");
+    if (ptr_location(Bbar_io) != PTR_DEVICE)
+      return fail(MPS_EINVAL, std::string(where) + ": Bbar must be device memory of the current device");
+  }
+  if (mode == RUN_END && w.shard_uid != c->uid)
+    return fail(MPS_EINVAL, "mps_energy_grad_shard_end: no mps_energy_grad_shard_begin with this circuit on this state");
   MPS_TRY(begin_call(s, 1 + 2 * (size_t)std::max(0, n_theta) + (gate_grad_out ? (size_t)c->n_gates : 0)));
   const double* d_theta = nullptr;
-  MPS_TRY(stage_theta(s, theta, n_theta, &d_theta));
+  if (mode != RUN_END) MPS_TRY(stage_theta(s, theta, n_theta, &d_theta));
   MPS_TRY(ensure_forward_scratch(L, w));
   MPS_TRY(ensure_gate_matrices(s, c));
   MPS_TRY(w.stats.ensure(10 * sizeof(double)));
@@ -1754,7 +1777,7 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
   };
   // Everything from the gate matrices to dE/dtheta, enqueued on the state's stream with no host
   // round trip, so that it can be captured once as a CUDA graph and replayed.
-  auto body = [&]() -> mps_status {
+  auto fwd_part = [&]() -> mps_status {
     gate_matrices_launch(s, c, d_theta, n_theta);
     MPS_TRY(w.work.copy_from(s->buf, L, s->st));
     if (nseg == 1) {
@@ -1771,6 +1794,10 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
     // energy and its cotangent
     MPS_TRY(energy_pass_impl(L, w.work, s->st, s->status.as<int>(), h, dE, nullptr, w.Bbar.as<double2>(),
                              s->cfg.precision == MPS_PRECISION_MIXED));
+    return MPS_OK;
+  };
+  auto rev_part = [&]() -> mps_status {
+    if (nseg == 1) layout_tapes(0, ng);   // the whole-circuit tape the forward pass recorded
     launch_zero_f64(cx.bt, w.lambar.as<double>(), L.lam_elems(), s->st);
     launch_zero_f64(cx.bt, w.gate_grad.as<double>(), std::max(1, ng), s->st);
     // reverse, segment by segment (re-running a segment's forward from its snapshot with a tape)
@@ -1793,6 +1820,29 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
     }
     return MPS_OK;
   };
+  auto body = [&]() -> mps_status {
+    MPS_TRY(fwd_part());
+    return rev_part();
+  };
+  if (mode == RUN_BEGIN) {   // this rank's energy and cotangent; the caller sums them over ranks
+    MPS_TRY(fwd_part());
+    launch_copy_f64(cx.bt, Bbar_io, bbar_doubles * sizeof(double), w.Bbar.as<double>(), cx.bt.stride, bbar_doubles,
+                    s->st);
+    MPS_TRY(put_out(s, E_out, dE, 1));
+    w.shard_uid = c->uid;
+    MPS_TRY(finish_call(s, where));
+    return harvest_profile(w);
+  }
+  if (mode == RUN_END) {     // the reverse pass from the summed cotangent
+    launch_copy_f64(cx.bt, w.Bbar.as<double>(), cx.bt.stride, Bbar_io, bbar_doubles * sizeof(double), bbar_doubles,
+                    s->st);
+    MPS_TRY(rev_part());
+    w.shard_uid = -1;
+    MPS_TRY(put_out(s, grad_out, w.grad.as<double>(), n_theta));
+    MPS_TRY(put_out(s, gate_grad_out, w.gate_grad.as<double>(), ng));
+    MPS_TRY(finish_call(s, where));
+    return harvest_profile(w);
+  }
   // The graph is valid while none of the buffers it touches has moved.
   const EnergyCache* ec = h->cache.get();
   std::vector<const void*> key = {(const void*)s->arena->uid, (const void*)c->uid, (const void*)h->uid,
@@ -1844,6 +1894,38 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
   MPS_TRY(put_out(s, gate_grad_out, w.gate_grad.as<double>(), ng));
   MPS_TRY(finish_call(s, "mps_energy_grad"));
   return harvest_profile(w);
+}
+
+}  // namespace mpsi
+
+extern "C" {
+
+mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const double* theta, int32_t n_theta,
+                               const mps_hamiltonian_dev* hc, double* E_out, double* grad_out,
+                               double* gate_grad_out) {
+  clear_error();
+  return energy_grad_run(RUN_FULL, s0, c, theta, n_theta, hc, E_out, grad_out, gate_grad_out, nullptr);
+}
+
+mps_status mps_energy_grad_shard_begin(const mps_state* s0, const mps_circuit* c, const double* theta,
+                                       int32_t n_theta, const mps_hamiltonian_dev* h_shard, double* E_out,
+                                       double* Bbar_out) {
+  clear_error();
+  return energy_grad_run(RUN_BEGIN, s0, c, theta, n_theta, h_shard, E_out, nullptr, nullptr, Bbar_out);
+}
+
+mps_status mps_energy_grad_shard_end(const mps_state* s0, const mps_circuit* c, int32_t n_theta,
+                                     const double* Bbar_in, double* grad_out, double* gate_grad_out) {
+  clear_error();
+  return energy_grad_run(RUN_END, s0, c, nullptr, n_theta, nullptr, nullptr, grad_out, gate_grad_out,
+                         const_cast<double*>(Bbar_in));
+}
+
+mps_status mps_cotangent_size(const mps_state* s, int64_t* n_doubles) {
+  clear_error();
+  if (!s || !n_doubles) return fail(MPS_EINVAL, "mps_cotangent_size: NULL argument");
+  *n_doubles = (int64_t)(2 * s->L.site_elems()) * s->n_inst();
+  return MPS_OK;
 }
 
 mps_status mps_energy_grad(const mps_state* s0, const mps_gate* gates, int32_t n_gates, const double* theta,

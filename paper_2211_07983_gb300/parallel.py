@@ -47,6 +47,23 @@ def shard_terms(x, z, c, world: int):
     return [np.array(sorted(o), dtype=np.int64) for o in out]
 
 
+def energy_grad_sharded(state0, circuit, theta, x, z, c, rank: int, world: int, allreduce=None):
+    """E and dE/dtheta of one instance with the strings split over `world` ranks (this is rank
+    `rank`): the forward and reverse passes are replicated, each rank sweeps its own strings, and
+    one sum-allreduce of (E_r, dE_r/dB*) joins them (mps_energy_grad_shard_begin / _end).
+
+    allreduce(list of tensors) sums in place over the ranks (default: torch.distributed SUM)."""
+    from . import api
+    idx = shard_terms(x, z, c, world)[rank]
+    x, z, c = np.asarray(x), np.asarray(z), np.asarray(c)
+    ham = api.Hamiltonian(state0.n, x[idx], z[idx], c[idx])
+    E, Bbar = api.energy_grad_shard_begin(state0, circuit, theta, ham)
+    (allreduce or allreduce_sum)([E, Bbar])
+    n_theta = int(np.asarray(theta).shape[-1]) if not hasattr(theta, "shape") else int(theta.shape[-1])
+    g = api.energy_grad_shard_end(state0, circuit, n_theta, Bbar)
+    return E, g
+
+
 def allreduce_sum(values, group=None):
     """Sum a list of torch tensors (or numpy arrays) over all ranks, in place for tensors."""
     import torch

@@ -737,3 +737,38 @@ def test_config2_doubles_against_oracle_values_and_32_central_differences(M):
     fd, ok = np.array(fd), np.array(ok)
     assert ok.sum() >= len(comps) - 4
     assert np.abs(fd[ok] - g[comps][ok]).max() <= 1e-7 * max(1.0, np.abs(g).max())
+
+
+def test_string_sharded_energy_grad_matches_the_whole_evaluation(M):
+    """mps_energy_grad_shard_begin / _end on one GPU with the strings split three ways: the
+    three ranks' (E_r, Bbar_r) summed (as the allreduce would) and one reverse pass give the
+    energy and gradient of the unsharded evaluation."""
+    import torch
+    from paper_2211_07983_gb300 import parallel
+    p = S.make_problem(1)
+    excs = p.excitations[:20]
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    gates = M.compile_excitations(p.n, excs)
+    circ = M.Circuit(p.n, gates)
+    th = p.theta[:20]
+    st = M.State.product(p.bits, p.spec.D, p.spec.eps, checkpoint_every=64)
+    E_ref, g_ref = M.energy_grad(st, circ, th, M.Hamiltonian(p.n, x, z, c))
+    world = 3
+    parts = []
+    for rank in range(world):
+        idx = parallel.shard_terms(x, z, c, world)[rank]
+        E_r, B_r = M.api.energy_grad_shard_begin(st, circ, th, M.Hamiltonian(p.n, x[idx], z[idx], c[idx]))
+        parts.append((E_r.clone(), B_r.clone()))
+    E = sum(e for e, _ in parts)
+    B = sum(b for _, b in parts)
+    g = M.api.energy_grad_shard_end(st, circ, len(th), B)
+    assert abs(E.item() - E_ref) <= 1e-12 * max(1.0, abs(E_ref))
+    assert np.linalg.norm(g - g_ref) <= 1e-11 * max(1.0, np.linalg.norm(g_ref))
+    # the same through the helper, with the allreduce replaced by the sum over the emulated ranks
+    def fake_allreduce(ts, rank_parts=parts):
+        ts[0].copy_(E)
+        ts[1].copy_(B)
+    E2, g2 = parallel.energy_grad_sharded(st, circ, th, x, z, c, 0, world, allreduce=fake_allreduce)
+    assert np.array_equal(g2, g)
+    with pytest.raises(M.api._lib.MpsError):      # end without a matching begin
+        M.api.energy_grad_shard_end(st, circ, len(th), B)
