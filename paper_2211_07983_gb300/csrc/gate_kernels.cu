@@ -492,6 +492,7 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(const SvdArgs p0, size
       p.tape_dims[2] = Dr;
       p.tape_dims[3] = k;
       p.tape_dims[4] = K;
+      p.tape_dims[5] = K < n ? k : 0;   // columns of the SVD adjoint's complement term
     }
     p.dims[b + 1] = k;
     if (p.stats) {   // device-side duration of this launch and of its phases

@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(256) zgemm_small_kernel(const GemmBatch batch,
   const int M = deval(d.M, d.dims), N = deval(d.N, d.dims), K = deval(d.K, d.dims);
   const int row0 = blockIdx.y * SM_T, col0 = blockIdx.x * SM_T;
   if (row0 >= M || col0 >= N || M <= 0 || N <= 0) return;
+  if (K <= 0 && d.beta.x == 1.0 && d.beta.y == 0.0) return;   // C = 0 + C: nothing to do
   const int lda = deval(d.lda, d.dims), ldb = deval(d.ldb, d.dims), ldc = deval(d.ldc, d.dims);
   __shared__ double2 As[SK][SM_T + 1];
   __shared__ double2 Bs[SK][SM_T + 1];

@@ -69,7 +69,9 @@ void launch_zero_f64(const Batch& bt, double* dst, size_t n, cudaStream_t st);
 // sweeps, FP64 re-orthonormalisation, FP64 sweeps; orthogonalises K = min(m, n) columns.
 // Writes s (K values, descending), Vs (K right singular vectors of length n, column j at
 // Vs + j*n), lam_out (slot b+1), dims[b+1] = k, and when non-null: W (K columns of length m,
-// W_j = C~ v_j, zero for numerical zeros), tape_dims {Dl, Dm, Dr, k, K}, lam_left_copy.
+// W_j = C~ v_j, zero for numerical zeros), tape_dims {Dl, Dm, Dr, k, K, kz} (kz = k when K < n,
+// else 0: the width of the adjoint's complement term, empty when the K vectors span C^n),
+// lam_left_copy.
 // scratch: global buffer of (K^2 + R K) complex values used when shared memory is too small.
 struct SvdArgs {
   const double2* A;

@@ -367,7 +367,7 @@ static mps_status reverse_gate(Ctx& cx, int t, int b, const TapeSlot& tp, double
   const Layout& L = *cx.L;
   Workspace& w = *cx.ws;
   const int* td = tp.dims;
-  const DimExpr m = dref(0, 2), Dm = dref(1), nc = dref(2, 2), k = dref(3), Ks = dref(4);
+  const DimExpr m = dref(0, 2), Dm = dref(1), nc = dref(2, 2), k = dref(3), Ks = dref(4), kz = dref(5);
   double2* Bbl = Bbar + L.site_off[b];
   double2* Bbr = Bbar + L.site_off[b + 1];
   const int mcap = 2 * L.cap[b], ncap = 2 * L.cap[b + 2], kcap = L.cap[b + 1], Kcap = std::min(mcap, ncap);
@@ -384,7 +384,16 @@ static mps_status reverse_gate(Ctx& cx, int t, int b, const TapeSlot& tp, double
   g.count = 1;
   g.d[0] = make_desc(td, tp.Vs, OP_C, w.Vbar, OP_N, w.Y, Ks, k, nc, nc, k, k);         // Y = V_e^H Vbar
   gemm_small(cx, g, Kcap, kcap, false);
-  g.d[0] = make_desc(td, tp.Vs, OP_T, w.Y, OP_N, w.Vbar, nc, k, Ks, nc, k, k, true, -1.0);   // Z = Vbar - V_e Y
+  // The complement Z = (I - V_e V_e^H) Vbar has kz = k columns when K < ncol and none when the K
+  // vectors span C^ncol (kz = 0: these GEMMs and the complement term below do nothing).
+  g.d[0] = make_desc(td, tp.Vs, OP_T, w.Y, OP_N, w.Vbar, nc, kz, Ks, nc, k, k, true, -1.0);   // Z = Vbar - V_e Y
+  gemm_small(cx, g, ncap, kcap, false);
+  // Z again minus its part in span(V_e): the subtraction above leaves rounding of size eps |Vbar|
+  // inside the span, which 1/w_k would amplify for small kept values; the second pass removes it
+  // (T1 is free until T1 = W K below).
+  g.d[0] = make_desc(td, tp.Vs, OP_C, w.Vbar, OP_N, w.T1, Ks, kz, nc, nc, k, k);       // Y2 = V_e^H Z
+  gemm_small(cx, g, Kcap, kcap, false);
+  g.d[0] = make_desc(td, tp.Vs, OP_T, w.T1, OP_N, w.Vbar, nc, kz, Ks, nc, k, k, true, -1.0);  // Z -= V_e Y2
   gemm_small(cx, g, ncap, kcap, false);
   launch_build_K(cx.bt, w.Y, tp.s, w.wbar, td, w.Km, Kcap, cx.st);                            // diag(wbar)+J+J^H
   launch_zscale(cx.bt, w.Vbar, tp.s, td, ncap, kcap, cx.st);                                  // Z diag(1/w_k)
@@ -392,7 +401,7 @@ static mps_status reverse_gate(Ctx& cx, int t, int b, const TapeSlot& tp, double
   gemm_small(cx, g, mcap, Kcap, false);
   g.d[0] = make_desc(td, w.T1, OP_N, tp.Vs, OP_C, w.Ctbar, m, nc, Ks, Ks, nc, nc);     // C~bar = T1 V_e^H
   gemm_small(cx, g, mcap, ncap, false);
-  g.d[0] = make_desc(td, tp.W, OP_T, w.Vbar, OP_H, w.Ctbar, m, nc, k, m, k, nc, true);  // += W_k (Z/w)^H
+  g.d[0] = make_desc(td, tp.W, OP_T, w.Vbar, OP_H, w.Ctbar, m, nc, kz, m, k, nc, true);  // += W_k (Z/w)^H
   gemm_small(cx, g, mcap, ncap, false);
   launch_lam_scale(cx.bt, w.Cbar, w.Ctbar, tp.C, tp.lamL, td, b > 0 ? lambar + L.lam_off[b] : nullptr, L.cap[b],
                    cx.st);

@@ -685,7 +685,8 @@ def test_config2_doubles_against_oracle_values_and_32_central_differences(M):
     """The differentiation workload (n = 20, D = 128, eps = 1e-10) on sixteen wide singles and six
     doubles (985 gates): bonds 10-12 reach D = 128 and truncation acts; the reverse pass runs two
     checkpoint segments of 512 gates.  E and dE/dtheta against the oracle's stored values
-    (tests/golden/make_config2_doubles.py), then central differences (h = 1e-5) on 32 angles
+    (tests/golden/make_config2_doubles.py; the gradient within 1e-9 relative or three times the
+    oracle's own rounding spread on this case, whichever is larger), then central differences (h = 1e-5) on 32 angles
     evaluated as 64 instances of batched states, against the reverse pass.  A component whose
     kept bond dimensions differ between theta +- h straddles a change of the truncation (the
     derivative is one-sided there) and is not compared; at most four may be skipped."""
@@ -708,7 +709,10 @@ def test_config2_doubles_against_oracle_values_and_32_central_differences(M):
     E, g, gg = M.energy_grad(st, circ, th, ham, gate_grad=True)
     g_ref = np.array(gold["grad"])
     assert abs(E - gold["E"]) <= E_TOL * max(1.0, abs(gold["E"]))
-    assert np.linalg.norm(g - g_ref) <= G_TOL * max(1.0, np.linalg.norm(g_ref))
+    # kept Schmidt values near 1e-9 s_1 make the FP64 gradient reproducible only to ~1e-9: the
+    # oracle itself moves by grad_spread_gesvd when LAPACK's other SVD driver computes its SVDs
+    g_tol = max(G_TOL, 3.0 * gold["grad_spread_gesvd"])
+    assert np.linalg.norm(g - g_ref) <= g_tol * max(1.0, np.linalg.norm(g_ref))
     st1 = M.State.product(p.bits, p.spec.D, p.spec.eps)
     M.apply_circuit(st1, circ, th)
     dims, _, _ = st1.read()
