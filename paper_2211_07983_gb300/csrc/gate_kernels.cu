@@ -117,8 +117,9 @@ __global__ void contract_kernel(const double2* __restrict__ Bl, const double2* _
 // of X0 = C~ are rotated (Q accumulates V), for m < n the m columns of X0 = C~^H (Q accumulates
 // U).  GB300 runs FP64 at 1/58 of its FP32 rate, so the sweeps first run in FP32 on a complex64
 // copy; the accumulated rotation is then re-orthonormalised in FP64 (modified Gram-Schmidt),
-// X = X0 Q is re-formed in FP64 from the untouched input, and FP64 sweeps finish to the FP64
-// convergence criterion.  The result is an FP64-accurate SVD whose FP64 work is a few sweeps.
+// X = X0 Q is re-formed in FP64 from the untouched input, and FP64 sweeps (scaled rotations,
+// numerically-zero columns cleaned first) finish to the FP64 convergence criterion.  The result
+// is an FP64-accurate SVD whose FP64 work is a few sweeps.
 // X, Q live in shared memory when they fit (the launcher decides), else in global scratch.
 constexpr int SVD_THREADS = 512;
 constexpr int SVD_MAX_SWEEPS = 60;
@@ -170,9 +171,10 @@ struct Cplx<float> {
 // 1/58 of the FP32 rate, and this keeps the divisions and square roots of a rotation in FP32.
 //
 // Stopping: a sweep that rotates nothing.  When `early` > 0, also a sweep whose largest rotated
-// |gamma|^2/(alpha beta) was <= early.  The FP64 phase passes early = (10 tol)^2: such a sweep
-// leaves inner products of order K (10 tol)^2, far below tol, so the confirming sweep would
-// rotate nothing.  (A looser bound, early = tol/(2K), was measured to cost 1e-9 in energies.)
+// |gamma|^2/(alpha beta) was <= early.  With early = (10 tol)^2 such a sweep leaves inner products
+// of order K (10 tol)^2, far below tol, so the confirming sweep would rotate nothing.  (A looser
+// bound, early = tol/(2K), was measured to cost 1e-9 in energies.)  This generic version runs the
+// FP32 phase; the FP64 phase uses the scaled variant below with the same rules.
 // Returns the number of sweeps run; *converged = 1 when a stopping rule was met.
 constexpr int JG = 8;   // lanes per column pair
 
@@ -303,6 +305,185 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
   return sweep;
 }
 
+// The FP64 sweeps, with the rotations applied in scaled form.  Each column carries a scale
+// d_j (and e_j = 1/d_j, kept as its own product so that no division is needed): the true column
+// is x_j = d_j xh_j.  The rotation a_p' = c (a_p - t e^{-i phi} a_q), a_q' = c (a_q + t e^{i phi} a_p)
+// then becomes xh_p' = xh_p - mu_p xh_q, xh_q' = xh_q + mu_q xh_p with mu_p = t (d_q e_p) e^{-i phi},
+// mu_q = t (d_p e_q) e^{i phi}, d_p' = c d_p, d_q' = c d_q: two FMAs per real output instead of
+// three, a third less work on GB300's FP64 pipe, which bounds this phase.  (This is the
+// square-root-free "fast Givens" idea applied to one-sided Jacobi.)  The scales start at 1 in every
+// sweep and are folded into X and Q at its end, so they never leave [0.7^K, 1].  For the small
+// rotations of this phase (t^2 < 1e-6) c = 1/sqrt(1 + t^2) and 1/c come from their Taylor series to
+// t^4 (error below t^6/3 < 4e-19); larger ones use the square root.
+//
+// Cleaning sweep: after the FP32 phase the numerically-zero columns of a rank-deficient C~ still
+// hold components of size ~1e-7 s_1 along the large singular vectors.  Rotating them against each
+// other while those components are being removed mixes them back in, and the sweeps converge only
+// linearly on them.  So when there are columns below clean_rel (1e-5) of the largest, the first
+// sweep skips the pairs of two such columns and only rotates them against the larger ones; every
+// later sweep rotates every pair.  (Skipping them in later sweeps too was tried: without their
+// mutual rotations a small kept column rotated against several of them can cycle without
+// converging.)
+//
+// Stopping: a sweep after the cleaning sweep that rotates nothing, or whose every rotated pair had
+// |gamma|^2 <= early alpha beta (early = (10 tol)^2: the next sweep would rotate nothing).
+__device__ int jacobi_sweeps_scaled(double2* X, double2* Q, int R, int K, double tol, double tiny, int max_sweeps,
+                                    int* flag_sh, int* notdone_sh, int* converged, double* nrm, double* dsc,
+                                    double* esc, double* maxn_sh, double* flops, double early, double clean_rel) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const int grp = lane / JG, gl = lane % JG, per_warp = 32 / JG;
+  const int Kp = K + (K & 1);
+  const double tol2 = tol * tol;
+  int sweep = 0;
+  long long checks = 0, rots = 0;
+  *converged = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    for (int j = warp; j < K; j += nwarp) {
+      double v = 0;
+      for (int i = lane; i < R; i += 32) {
+        const double2 x = X[(size_t)j * R + i];
+        v += x.x * x.x + x.y * x.y;
+      }
+      v = warp_sum(v);
+      if (lane == 0) {
+        nrm[j] = v;
+        dsc[j] = 1.0;
+        esc[j] = 1.0;
+      }
+    }
+    if (tid == 0) {
+      *flag_sh = 0;
+      *notdone_sh = 0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double mx = 0.0;
+      for (int j = lane; j < K; j += 32) mx = fmax(mx, nrm[j]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) *maxn_sh = mx;
+    }
+    __syncthreads();
+    const double maxn = *maxn_sh;
+    // the cleaning rule applies to the first sweep, and only when there is something to clean
+    bool cleaning = false;
+    if (sweep == 0) {
+      int any_small = 0;
+      for (int j = tid; j < K; j += blockDim.x) any_small |= nrm[j] >= tiny && nrm[j] < clean_rel * clean_rel * maxn;
+      cleaning = __syncthreads_or(any_small) != 0;
+    }
+    const double thr = cleaning ? clean_rel * clean_rel * maxn : 0.0;
+    for (int r = 0; r < Kp - 1; ++r) {
+      for (int t0 = warp * per_warp; t0 < Kp / 2; t0 += nwarp * per_warp) {   // uniform over the warp
+        const int t = t0 + grp;
+        int pc = 0, qc = 0;
+        bool live = t < Kp / 2;
+        if (live) {
+          if (t == 0) {
+            pc = r;
+            qc = Kp - 1;
+          } else {
+            pc = (r + t) % (Kp - 1);
+            qc = (r - t + Kp - 1) % (Kp - 1);
+          }
+          live = pc < K && qc < K;
+        }
+        double al = 0, be = 0;
+        if (live) {
+          al = nrm[pc];
+          be = nrm[qc];
+          live = !(al < tiny || be < tiny) && !(al < thr && be < thr);
+        }
+        double2* ap = X + (size_t)pc * R;
+        double2* aq = X + (size_t)qc * R;
+        double gr = 0, gi = 0;
+        if (live) {
+          for (int i = gl; i < R; i += JG) {
+            const double2 x = ap[i], y = aq[i];
+            gr = fma(x.x, y.x, gr);   // conj(x) y
+            gr = fma(x.y, y.y, gr);
+            gi = fma(x.x, y.y, gi);
+            gi = fma(-x.y, y.x, gi);
+          }
+        }
+        gr = group_sum(gr);   // every lane of the warp takes part in the shuffles
+        gi = group_sum(gi);
+        if (!live) continue;
+        if (gl == 0) ++checks;
+        const double dp = dsc[pc], dq = dsc[qc], dd = dp * dq;
+        gr *= dd;   // inner product of the true columns
+        gi *= dd;
+        const double g2 = gr * gr + gi * gi;
+        const double ab = al * be;
+        if (!(g2 > tol2 * ab)) continue;
+        const double inv_g = rsqrt(g2);
+        const double g = g2 * inv_g;
+        const float zf = (float)((be - al) * (0.5 * inv_g));
+        const float af = fabsf(zf);
+        const float tf = af > 1e15f ? 0.5f / zf : copysignf(1.f / (af + sqrtf(1.f + zf * zf)), zf);
+        const double tt = (double)tf;
+        const double t2 = tt * tt;
+        double c, rc;   // c = 1/sqrt(1 + t^2), rc = 1/c
+        if (t2 < 1e-6) {
+          c = fma(t2, fma(0.375, t2, -0.5), 1.0);
+          rc = fma(t2, fma(-0.125, t2, 0.5), 1.0);
+        } else {
+          c = rsqrt(1.0 + t2);
+          rc = (1.0 + t2) * c;
+        }
+        const double ep = esc[pc], eq = esc[qc];
+        const double kp = tt * (dq * ep) * inv_g, kq = tt * (dp * eq) * inv_g;
+        const double mpr = kp * gr, mpi = -kp * gi;   // mu_p = t (d_q/d_p) e^{-i phi}
+        const double mqr = kq * gr, mqi = kq * gi;    // mu_q = t (d_p/d_q) e^{i phi}
+        for (int i = gl; i < R; i += JG) {
+          const double2 x = ap[i], y = aq[i];
+          ap[i] = make_double2(fma(-mpr, y.x, fma(mpi, y.y, x.x)), fma(-mpr, y.y, fma(-mpi, y.x, x.y)));
+          aq[i] = make_double2(fma(mqr, x.x, fma(-mqi, x.y, y.x)), fma(mqr, x.y, fma(mqi, x.x, y.y)));
+        }
+        double2* vp = Q + (size_t)pc * K;
+        double2* vq = Q + (size_t)qc * K;
+        for (int i = gl; i < K; i += JG) {
+          const double2 x = vp[i], y = vq[i];
+          vp[i] = make_double2(fma(-mpr, y.x, fma(mpi, y.y, x.x)), fma(-mpr, y.y, fma(-mpi, y.x, x.y)));
+          vq[i] = make_double2(fma(mqr, x.x, fma(-mqi, x.y, y.x)), fma(mqr, x.y, fma(mqi, x.x, y.y)));
+        }
+        if (gl == 0) {
+          ++rots;
+          nrm[pc] = al - tt * g;
+          nrm[qc] = be + tt * g;
+          dsc[pc] = dp * c;
+          dsc[qc] = dq * c;
+          esc[pc] = ep * rc;
+          esc[qc] = eq * rc;
+          *flag_sh = 1;
+          if (g2 > early * ab) *notdone_sh = 1;
+        }
+      }
+      __syncthreads();
+    }
+    // fold the scales into the columns
+    for (int e = tid; e < R * K; e += blockDim.x) X[e] = cscale(X[e], dsc[e / R]);
+    for (int e = tid; e < K * K; e += blockDim.x) Q[e] = cscale(Q[e], dsc[e / K]);
+    __syncthreads();
+    const int rot = *flag_sh, nd = *notdone_sh;
+    __syncthreads();
+    if (!cleaning && (!rot || !nd)) {
+      *converged = 1;
+      ++sweep;
+      break;
+    }
+  }
+  // work done: per sweep K column norms (4R flops each) and the scale fold (2(R+K) per column), per
+  // checked pair one complex inner product (8R), per rotation the scaled update of two columns of
+  // X (16R) and of Q (16K)
+  if (flops && gl == 0 && (checks | rots)) {
+    const double f = 8.0 * R * (double)checks + (16.0 * R + 16.0 * K) * (double)rots;
+    atomicAdd(flops, f);
+  }
+  if (flops && tid == 0) atomicAdd(flops, (4.0 * R * K + 2.0 * (R + K) * K) * (double)sweep);
+  return sweep;
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -330,7 +511,9 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(const SvdArgs p0, size
   }
   __shared__ double red[SVD_THREADS / 32];
   __shared__ double s_sh[512];
-  __shared__ int flag_sh, conv_sh, k_sh;
+  __shared__ double dsc_sh[512], esc_sh[512];   // column scales of the FP64 sweeps
+  __shared__ int flag_sh, conv_sh, k_sh, notdone_sh;
+  __shared__ double maxn_sh;
   __shared__ unsigned long long maxrel_sh;
   __shared__ double fro2_sh, smax_sh, nk_sh;
   const int b = p.b;
@@ -373,18 +556,21 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(const SvdArgs p0, size
                            0.0, &maxrel_sh);
   const unsigned long long t_fp32 = global_ns();
   // ---- Q64 = orthonormalised Q32 (modified Gram-Schmidt, FP64) ----
+  // Column j + 1 is final once it has been projected against column j; the warp that projects it
+  // (warp 0) normalises it in the same step, so each column costs one barrier.
+  auto normalise = [&](double2* q) {   // one warp
+    double v = 0.0;
+    for (int i = lane; i < K; i += 32) v += q[i].x * q[i].x + q[i].y * q[i].y;
+    v = warp_sum(v);
+    const double inv = 1.0 / sqrt(v);
+    for (int i = lane; i < K; i += 32) q[i] = cscale(q[i], inv);
+  };
   for (int e = tid; e < K * K; e += SVD_THREADS) Q64[e] = make_double2((double)Q32[e].x, (double)Q32[e].y);
   __syncthreads();
-  for (int j = 0; j < K; ++j) {
-    double2* qj = Q64 + (size_t)j * K;
-    if (warp == 0) {
-      double v = 0.0;
-      for (int i = lane; i < K; i += 32) v += qj[i].x * qj[i].x + qj[i].y * qj[i].y;
-      v = warp_sum(v);
-      const double inv = 1.0 / sqrt(v);
-      for (int i = lane; i < K; i += 32) qj[i] = cscale(qj[i], inv);
-    }
-    __syncthreads();
+  if (warp == 0) normalise(Q64);
+  __syncthreads();
+  for (int j = 0; j + 1 < K; ++j) {
+    const double2* qj = Q64 + (size_t)j * K;
     for (int l = j + 1 + warp; l < K; l += nwarp) {
       double2* ql = Q64 + (size_t)l * K;
       double pr = 0.0, pim = 0.0;
@@ -396,23 +582,45 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(const SvdArgs p0, size
       pim = warp_sum(pim);
       const double2 d = make_double2(pr, pim);
       for (int i = lane; i < K; i += 32) ql[i] = csub(ql[i], cmul(d, qj[i]));
+      if (l == j + 1) normalise(ql);   // each lane rescales the entries it wrote
     }
     __syncthreads();
   }
   // ---- X64 = X0 Q64 (FP64, from the untouched input) ----
-  for (int e = tid; e < R * K; e += SVD_THREADS) {
-    const int j = e / R, r = e % R;
-    const double2* qj = Q64 + (size_t)j * K;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int l = 0; l < K; ++l) acc = cfma(x0(r, l), qj[l], acc);
-    X64[(size_t)j * R + r] = acc;
+  // A thread forms four columns of one row, so each element of X0 is loaded once per four
+  // complex FMAs and the four accumulations are independent.
+  {
+    constexpr int JB = 4;
+    const int nb = (K + JB - 1) / JB;
+    for (int e = tid; e < R * nb; e += SVD_THREADS) {
+      const int j0 = (e / R) * JB, r = e % R;
+      double2 acc[JB];
+#pragma unroll
+      for (int u = 0; u < JB; ++u) acc[u] = make_double2(0.0, 0.0);
+      if (j0 + JB <= K) {
+        for (int l = 0; l < K; ++l) {
+          const double2 a = x0(r, l);
+#pragma unroll
+          for (int u = 0; u < JB; ++u) acc[u] = cfma(a, Q64[(size_t)(j0 + u) * K + l], acc[u]);
+        }
+      } else {
+        for (int l = 0; l < K; ++l) {
+          const double2 a = x0(r, l);
+          for (int u = 0; u < JB && j0 + u < K; ++u) acc[u] = cfma(a, Q64[(size_t)(j0 + u) * K + l], acc[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < JB; ++u)
+        if (j0 + u < K) X64[(size_t)(j0 + u) * R + r] = acc[u];
+    }
   }
   __syncthreads();
   // ---- FP64 sweeps ----
   const unsigned long long t_reform = global_ns();
   const double tol64 = 4.0 * 2.220446049250313e-16 * sqrt((double)R);
-  const int sweeps64 = jacobi_sweeps<double>(X64, Q64, R, K, tol64, 1e-30 * fro2_sh, SVD_MAX_SWEEPS, &flag_sh,
-                                             &conv_sh, s_sh, p.stats, 100.0 * tol64 * tol64, &maxrel_sh);
+  const int sweeps64 = jacobi_sweeps_scaled(X64, Q64, R, K, tol64, 1e-30 * fro2_sh, SVD_MAX_SWEEPS, &flag_sh,
+                                            &notdone_sh, &conv_sh, s_sh, dsc_sh, esc_sh, &maxn_sh, p.stats,
+                                            100.0 * tol64 * tol64, 1e-5);
   const unsigned long long t_fp64 = global_ns();
   // FP64 work outside the sweeps: Gram-Schmidt (~8 K^3) and X = X0 Q (8 R K^2)
   if (p.stats && tid == 0) atomicAdd(p.stats, 8.0 * K * K * (double)K + 8.0 * R * K * (double)K);
