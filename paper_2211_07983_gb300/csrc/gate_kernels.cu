@@ -170,25 +170,24 @@ struct Cplx<float> {
 // sweep at no extra sweep count, since the sweeps converge quadratically).  FP64 on GB300 runs at
 // 1/58 of the FP32 rate, and this keeps the divisions and square roots of a rotation in FP32.
 //
-// Stopping: a sweep that rotates nothing.  When `early` > 0, also a sweep whose largest rotated
-// |gamma|^2/(alpha beta) was <= early.  With early = (10 tol)^2 such a sweep leaves inner products
-// of order K (10 tol)^2, far below tol, so the confirming sweep would rotate nothing.  (A looser
-// bound, early = tol/(2K), was measured to cost 1e-9 in energies.)  This generic version runs the
-// FP32 phase; the FP64 phase uses the scaled variant below with the same rules.
+// Stopping: a sweep that rotates nothing.  This generic version runs the FP32 phase; the FP64
+// phase uses the scaled variant below, which also stops early.
 // Returns the number of sweeps run; *converged = 1 when a stopping rule was met.
-constexpr int JG = 8;   // lanes per column pair
-
-template <class T>
+//
+// JG (lanes per column pair, 8, 16 or 32) is chosen by the caller from the number of pairs in a
+// round, so that a round's pairs spread over every warp scheduler of the SM: with few pairs, more
+// lanes per pair shorten each lane's serial loop and bring more warps (FP32 phase, latency bound)
+// or more of the four FP64 pipes (FP64 phase) into use.
+template <int JG, class T>
 __device__ __forceinline__ T group_sum(T v) {
 #pragma unroll
   for (int o = JG / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-template <class T>
+template <class T, int JG>
 __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int R, int K, T tol, T tiny,
-                             int max_sweeps, int* flag_sh, int* converged, T* nrm, double* flops,
-                             double early, unsigned long long* maxrel_sh) {
+                             int max_sweeps, int* flag_sh, int* converged, T* nrm, double* flops) {
   using C2 = typename Cplx<T>::t;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   const int grp = lane / JG, gl = lane % JG, per_warp = 32 / JG;
@@ -209,10 +208,8 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
     }
     if (tid == 0) {
       *flag_sh = 0;
-      *maxrel_sh = 0ull;
     }
     __syncthreads();
-    double maxrel = 0.0;   // this group's largest rotated |gamma|^2/(alpha beta) in this sweep
     for (int r = 0; r < Kp - 1; ++r) {
       for (int t0 = warp * per_warp; t0 < Kp / 2; t0 += nwarp * per_warp) {   // uniform over the warp
         const int t = t0 + grp;
@@ -244,8 +241,8 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
             gi += x.x * y.y - x.y * y.x;
           }
         }
-        gr = group_sum(gr);   // every lane of the warp takes part in the shuffles
-        gi = group_sum(gi);
+        gr = group_sum<JG>(gr);   // every lane of the warp takes part in the shuffles
+        gi = group_sum<JG>(gi);
         if (!live) continue;
         if (gl == 0) ++checks;
         const T g2 = gr * gr + gi * gi;
@@ -259,7 +256,6 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
         const T tt = (T)tf;
         const T c = rsqrt(T(1) + tt * tt), s = c * tt;
         const T pr = gr * inv_g, pim = gi * inv_g;                 // e^{i phi}
-        maxrel = fmax(maxrel, (double)(g2 / ab));
         // a_p' = c a_p - s e^{-i phi} a_q ; a_q' = s e^{i phi} a_p + c a_q
         const T spr = s * pr, spi = s * pim;
         for (int i = gl; i < R; i += JG) {
@@ -283,13 +279,9 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
       }
       __syncthreads();
     }
-    // largest rotation of the sweep (non-negative doubles order like their bit patterns)
-    if (gl == 0 && maxrel > 0.0) atomicMax(maxrel_sh, (unsigned long long)__double_as_longlong(maxrel));
-    __syncthreads();
     const int rot = *flag_sh;
-    const double mr = __longlong_as_double((long long)*maxrel_sh);
     __syncthreads();
-    if (!rot || (early > 0.0 && mr <= early)) {
+    if (!rot) {
       *converged = 1;
       ++sweep;
       break;
@@ -326,7 +318,10 @@ __device__ int jacobi_sweeps(typename Cplx<T>::t* X, typename Cplx<T>::t* Q, int
 // converging.)
 //
 // Stopping: a sweep after the cleaning sweep that rotates nothing, or whose every rotated pair had
-// |gamma|^2 <= early alpha beta (early = (10 tol)^2: the next sweep would rotate nothing).
+// |gamma|^2 <= early alpha beta.  With early = (10 tol)^2 such a sweep leaves inner products of
+// order K (10 tol)^2, far below tol, so the confirming sweep would rotate nothing.  (A looser
+// bound, early = tol/(2K), was measured to cost 1e-9 in energies.)
+template <int JG>
 __device__ int jacobi_sweeps_scaled(double2* X, double2* Q, int R, int K, double tol, double tiny, int max_sweeps,
                                     int* flag_sh, int* notdone_sh, int* converged, double* nrm, double* dsc,
                                     double* esc, double* maxn_sh, double* flops, double early, double clean_rel) {
@@ -406,8 +401,8 @@ __device__ int jacobi_sweeps_scaled(double2* X, double2* Q, int R, int K, double
             gi = fma(-x.y, y.x, gi);
           }
         }
-        gr = group_sum(gr);   // every lane of the warp takes part in the shuffles
-        gi = group_sum(gi);
+        gr = group_sum<JG>(gr);   // every lane of the warp takes part in the shuffles
+        gi = group_sum<JG>(gi);
         if (!live) continue;
         if (gl == 0) ++checks;
         const double dp = dsc[pc], dq = dsc[qc], dd = dp * dq;
@@ -514,7 +509,6 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(const SvdArgs p0, size
   __shared__ double dsc_sh[512], esc_sh[512];   // column scales of the FP64 sweeps
   __shared__ int flag_sh, conv_sh, k_sh, notdone_sh;
   __shared__ double maxn_sh;
-  __shared__ unsigned long long maxrel_sh;
   __shared__ double fro2_sh, smax_sh, nk_sh;
   const int b = p.b;
   const int Dl = p.dims[b], Dr = p.dims[b + 2];
@@ -550,41 +544,72 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(const SvdArgs p0, size
   }
   __syncthreads();
   int conv = 0;
-  const int sweeps32 =
-      jacobi_sweeps<float>(X32, Q32, R, K, 4.f * 1.1920929e-7f * sqrtf((float)R), (float)(1e-30 * fro2_sh) + 1e-37f,
-                           30, &flag_sh, &conv, reinterpret_cast<float*>(s_sh), p.stats ? p.stats + 1 : nullptr,
-                           0.0, &maxrel_sh);
+  const int npairs = (K + (K & 1)) / 2;   // column pairs per round
+  int sweeps32 = 0;
+  {
+    const float tol32 = 4.f * 1.1920929e-7f * sqrtf((float)R), tiny32 = (float)(1e-30 * fro2_sh) + 1e-37f;
+    float* nrm32 = reinterpret_cast<float*>(s_sh);
+    double* fl32 = p.stats ? p.stats + 1 : nullptr;
+    if (npairs <= 16)
+      sweeps32 = jacobi_sweeps<float, 32>(X32, Q32, R, K, tol32, tiny32, 30, &flag_sh, &conv, nrm32, fl32);
+    else if (npairs <= 32)
+      sweeps32 = jacobi_sweeps<float, 16>(X32, Q32, R, K, tol32, tiny32, 30, &flag_sh, &conv, nrm32, fl32);
+    else
+      sweeps32 = jacobi_sweeps<float, 8>(X32, Q32, R, K, tol32, tiny32, 30, &flag_sh, &conv, nrm32, fl32);
+  }
   const unsigned long long t_fp32 = global_ns();
   // ---- Q64 = orthonormalised Q32 (modified Gram-Schmidt, FP64) ----
-  // Column j + 1 is final once it has been projected against column j; the warp that projects it
-  // (warp 0) normalises it in the same step, so each column costs one barrier.
-  auto normalise = [&](double2* q) {   // one warp
-    double v = 0.0;
-    for (int i = lane; i < K; i += 32) v += q[i].x * q[i].x + q[i].y * q[i].y;
-    v = warp_sum(v);
-    const double inv = 1.0 / sqrt(v);
-    for (int i = lane; i < K; i += 32) q[i] = cscale(q[i], inv);
-  };
-  for (int e = tid; e < K * K; e += SVD_THREADS) Q64[e] = make_double2((double)Q32[e].x, (double)Q32[e].y);
-  __syncthreads();
-  if (warp == 0) normalise(Q64);
-  __syncthreads();
-  for (int j = 0; j + 1 < K; ++j) {
-    const double2* qj = Q64 + (size_t)j * K;
-    for (int l = j + 1 + warp; l < K; l += nwarp) {
-      double2* ql = Q64 + (size_t)l * K;
-      double pr = 0.0, pim = 0.0;
-      for (int i = lane; i < K; i += 32) {   // qj^H ql
-        pr += qj[i].x * ql[i].x + qj[i].y * ql[i].y;
-        pim += qj[i].x * ql[i].y - qj[i].y * ql[i].x;
-      }
-      pr = warp_sum(pr);
-      pim = warp_sum(pim);
-      const double2 d = make_double2(pr, pim);
-      for (int i = lane; i < K; i += 32) ql[i] = csub(ql[i], cmul(d, qj[i]));
-      if (l == j + 1) normalise(ql);   // each lane rescales the entries it wrote
+  // A column is handled by a group of 8 lanes (4 columns per warp), so an inner product costs
+  // three shuffle-and-add steps shared by four columns rather than five per column: on GB300 each
+  // of those adds occupies the FP64 pipe as long as a multiply-add.  Column j + 1 is final once it
+  // has been projected against column j; warp 0, which projects it, normalises it in the same
+  // step, so each column costs one barrier.
+  {
+    constexpr int MG = 8;
+    const int grp = lane / MG, gl = lane % MG, gpw = 32 / MG;
+    for (int e = tid; e < K * K; e += SVD_THREADS) Q64[e] = make_double2((double)Q32[e].x, (double)Q32[e].y);
+    __syncthreads();
+    if (warp == 0) {   // column 0
+      double v = 0.0;
+      for (int i = lane; i < K; i += 32) v += Q64[i].x * Q64[i].x + Q64[i].y * Q64[i].y;
+      v = warp_sum(v);
+      const double inv = rsqrt(v);
+      for (int i = lane; i < K; i += 32) Q64[i] = cscale(Q64[i], inv);
     }
     __syncthreads();
+    for (int j = 0; j + 1 < K; ++j) {
+      const double2* qj = Q64 + (size_t)j * K;
+      for (int l0 = j + 1 + warp * gpw; l0 < K; l0 += nwarp * gpw) {   // uniform over the warp
+        const int l = l0 + grp;
+        const bool live = l < K;
+        double2* ql = Q64 + (size_t)(live ? l : j) * K;
+        double pr = 0.0, pim = 0.0;
+        if (live)
+          for (int i = gl; i < K; i += MG) {   // qj^H ql
+            const double2 a = qj[i], b = ql[i];
+            pr = fma(a.x, b.x, fma(a.y, b.y, pr));
+            pim = fma(a.x, b.y, fma(-a.y, b.x, pim));
+          }
+        pr = group_sum<MG>(pr);
+        pim = group_sum<MG>(pim);
+        if (live)
+          for (int i = gl; i < K; i += MG) {
+            const double2 a = qj[i], b = ql[i];
+            ql[i] = make_double2(b.x - (pr * a.x - pim * a.y), b.y - (pr * a.y + pim * a.x));
+          }
+        if (l0 == j + 1) {   // warp 0: normalise column j + 1 (group 0); each lane rescales its own entries
+          double v = 0.0;
+          if (live)
+            for (int i = gl; i < K; i += MG) v += ql[i].x * ql[i].x + ql[i].y * ql[i].y;
+          v = group_sum<MG>(v);
+          if (grp == 0) {
+            const double inv = rsqrt(v);
+            for (int i = gl; i < K; i += MG) ql[i] = cscale(ql[i], inv);
+          }
+        }
+      }
+      __syncthreads();
+    }
   }
   // ---- X64 = X0 Q64 (FP64, from the untouched input) ----
   // A thread forms four columns of one row, so each element of X0 is loaded once per four
@@ -618,9 +643,19 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(const SvdArgs p0, size
   // ---- FP64 sweeps ----
   const unsigned long long t_reform = global_ns();
   const double tol64 = 4.0 * 2.220446049250313e-16 * sqrt((double)R);
-  const int sweeps64 = jacobi_sweeps_scaled(X64, Q64, R, K, tol64, 1e-30 * fro2_sh, SVD_MAX_SWEEPS, &flag_sh,
-                                            &notdone_sh, &conv_sh, s_sh, dsc_sh, esc_sh, &maxn_sh, p.stats,
-                                            100.0 * tol64 * tol64, 1e-5);
+  int sweeps64 = 0;
+  {
+    const double tiny64 = 1e-30 * fro2_sh, early64 = 100.0 * tol64 * tol64;
+    if (npairs <= 4)
+      sweeps64 = jacobi_sweeps_scaled<32>(X64, Q64, R, K, tol64, tiny64, SVD_MAX_SWEEPS, &flag_sh, &notdone_sh,
+                                          &conv_sh, s_sh, dsc_sh, esc_sh, &maxn_sh, p.stats, early64, 1e-5);
+    else if (npairs <= 8)
+      sweeps64 = jacobi_sweeps_scaled<16>(X64, Q64, R, K, tol64, tiny64, SVD_MAX_SWEEPS, &flag_sh, &notdone_sh,
+                                          &conv_sh, s_sh, dsc_sh, esc_sh, &maxn_sh, p.stats, early64, 1e-5);
+    else
+      sweeps64 = jacobi_sweeps_scaled<8>(X64, Q64, R, K, tol64, tiny64, SVD_MAX_SWEEPS, &flag_sh, &notdone_sh,
+                                         &conv_sh, s_sh, dsc_sh, esc_sh, &maxn_sh, p.stats, early64, 1e-5);
+  }
   const unsigned long long t_fp64 = global_ns();
   // FP64 work outside the sweeps: Gram-Schmidt (~8 K^3) and X = X0 Q (8 R K^2)
   if (p.stats && tid == 0) atomicAdd(p.stats, 8.0 * K * K * (double)K + 8.0 * R * K * (double)K);
