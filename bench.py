@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     ap.add_argument("--no-n40", action="store_true", help="skip the n = 40, D = 256 measurements")
     ap.add_argument("--no-psr", action="store_true", help="skip the parameter-shift comparison")
+    ap.add_argument("--config3", action="store_true",
+                    help="also run the 64-instance uneven batch (about 15 minutes: looped single calls "
+                         "against mps_energy_grad_multi)")
     ap.add_argument("--profile-case", default=None,
                     choices=["zgemm_tc", "zgemm_mma_sync", "zgemm_fp64", "svd_coop", "step"],
                     help="run one kernel on a synthetic case (two warm-up calls, one timed) for a profiler "
@@ -370,6 +373,50 @@ def run_psr(M, stream):
                     "(2 M_rz forward passes and energies, 256 instances per batched state)"}
 
 
+def run_config3(M, n_single=8, n_double=4):
+    """The batching workload: 64 independent problems of uneven (n, D), each with its own seeded
+    Hamiltonian and a seeded sample of its singles-and-doubles ansatz (n_single singles and
+    n_double doubles; the whole ansatz of the larger instances is out of reach, as at n = 40),
+    evaluated (a) one mps_energy_grad call after another and (b) all together through
+    mps_energy_grad_multi (one library stream per problem, each replaying its own captured graph).
+    Both timed by the host clock around whole calls, after warm-up calls that allocate and capture."""
+    import torch
+    probs = []
+    for i in range(64):
+        p = S.make_problem(3, i)
+        excs = S.sampled_excitations(p.excitations, n_single, n_double, S.seed_for(3, 20_000 + i))
+        x, z, c = M.build_hamiltonian(p.h, p.eri)
+        st = M.State.product(p.bits, p.spec.D, p.spec.eps, checkpoint_every=256)
+        st.set_svd_policy(True)   # one CTA per SVD: many problems share the GPU
+        gates = M.compile_excitations(p.n, excs)
+        probs.append((st, M.Circuit(p.n, gates), p.theta[: len(excs)], M.Hamiltonian(p.n, x, z, c),
+                      p.n, p.spec.D, len(gates), len(x)))
+    states, circs, thetas, hams = (list(v) for v in zip(*[q[:4] for q in probs]))
+    single = [M.energy_grad(st, c, th, h) for st, c, th, h in zip(states, circs, thetas, hams)]   # eager
+    for _ in range(2):   # the second call captures each problem's graph
+        M.energy_grad_multi(states, circs, thetas, hams)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loop = [M.energy_grad(st, c, th, h) for st, c, th, h in zip(states, circs, thetas, hams)]
+    t_loop = time.perf_counter() - t0
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        Es, gs = M.energy_grad_multi(states, circs, thetas, hams)
+    t_multi = (time.perf_counter() - t0) / reps
+    same = all(Es[k] == loop[k][0] and np.array_equal(gs[k], loop[k][1]) for k in range(64))
+    for st in states:
+        st.free()
+    return {"workload": f"64 instances: n in {{8..28}}, D in {{16..256}} (capped at 2^(n/2)), eps=1e-10; "
+                        f"{n_single} singles + {n_double} doubles sampled per instance; "
+                        f"{sum(q[6] for q in probs)} gates and {sum(q[7] for q in probs)} Pauli strings in all",
+            "instances": [{"n": q[4], "D": q[5], "gates": q[6], "strings": q[7]} for q in probs],
+            "loop_single_s": t_loop, "multi_s": t_multi,
+            "loop_evals_per_s": 64 / t_loop, "multi_evals_per_s": 64 / t_multi, "speedup": t_loop / t_multi,
+            "multi_equals_single_bitwise": bool(same),
+            "note": "host wall clock around whole calls (each call synchronises); SVD policy one CTA per matrix"}
+
+
 def run_ours(args, rank, world, local):
     import torch
     import paper_2211_07983_gb300 as M
@@ -511,6 +558,9 @@ def run_ours(args, rank, world, local):
     psr_rows = None
     if rank == 0 and not args.no_psr:
         psr_rows = run_psr(M, stream)
+    batch64 = None
+    if rank == 0 and args.config3:
+        batch64 = run_config3(M)
     # ---- roofline of the dominant kernel (the gate SVD: one CTA per instance per launch) ----
     roof = None
     n_launch = prof["svd_launches"]
@@ -546,7 +596,7 @@ def run_ours(args, rank, world, local):
                                       "roofline": energy_roof,
                                       "note": f"energy pass alone on the {B} final states ({len(x)} strings each), "
                                               "best of 3 calls timed with CUDA events"},
-                "n40_D256": n40, "psr": psr_rows}
+                "n40_D256": n40, "psr": psr_rows, "batch64_uneven": batch64}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

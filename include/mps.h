@@ -235,6 +235,39 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
                                double* grad_out, double* gate_grad_out);
 
 /*
+ * Which SVD a single-instance state's gates use.  MPS_SVD_AUTO (the default): a gate whose
+ * two-site matrix can exceed 128 rows or columns (bond caps above 64) runs the cooperative SVD,
+ * which spreads one matrix over every SM; smaller ones, and every gate of a batched state, run one
+ * CTA per matrix.  MPS_SVD_ONE_CTA: always one CTA per matrix (its work arrays in global memory
+ * when they exceed shared memory), for callers that run many problems at once
+ * (mps_energy_grad_multi), where one SM per problem keeps the GPU full and a whole-GPU SVD would
+ * have to run alone.  Results agree with the other policy to rounding.  MPS_EINVAL for a NULL
+ * state or an unknown policy.
+ */
+enum { MPS_SVD_AUTO = 0, MPS_SVD_ONE_CTA = 1 };
+mps_status mps_set_svd_policy(mps_state* s, int32_t policy);
+
+/*
+ * E and dE/dtheta of n_prob independent problems of uneven size (their own qubit counts, bond
+ * dimensions, circuits and Hamiltonians), evaluated together: problem i is exactly
+ * mps_energy_grad_dev(states[i], circuits[i], theta[i], n_theta[i], hams[i], E_out[i],
+ * grad_out[i], NULL), with the same results bit for bit.  The problems whose SVDs fit one CTA
+ * (every two-site matrix at most 128 on a side, or batched states) are enqueued on one
+ * library-owned stream each, so the GPU runs them concurrently, and each replays its own captured
+ * graph from its third evaluation on; the problems that need the cooperative whole-GPU SVD run
+ * afterwards, one at a time.  Each problem's work starts after the work already enqueued on its
+ * state's stream, and the call returns when every problem has finished.  E_out[i], grad_out[i]:
+ * host or device, n_inst and n_inst * n_theta[i] doubles.  Errors: MPS_EINVAL for NULL arguments,
+ * n_prob < 1 or a state passed twice; otherwise the first failing problem's status and message
+ * (the others are still waited for).  No counterpart in the paper; this is the batching of
+ * independent instances of uneven size.
+ */
+mps_status mps_energy_grad_multi(int32_t n_prob, mps_state* const* states, const mps_circuit* const* circuits,
+                                 const double* const* theta, const int32_t* n_theta,
+                                 const mps_hamiltonian_dev* const* hams, double* const* E_out,
+                                 double* const* grad_out);
+
+/*
  * E and dE/dtheta with the Pauli strings split over processes (one process per GPU).  E and the
  * energy cotangent dE/dB* are linear in the strings once divided by the common <psi|psi>
  * (Sec. 2, Eq. expect-val; Sec. 4, Eq. expecgrad): with H = sum_r H_r, E = sum_r E_r and

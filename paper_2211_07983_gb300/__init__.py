@@ -7,9 +7,9 @@ include/mps.h).  This package holds its ctypes binding (`api`), the autograd wra
 and fails loudly if the library was not built.
 """
 from .api import (Circuit, Hamiltonian, State, apply_circuit, apply_circuit_host, build_hamiltonian,
-                  compile_excitations, energy, energy_cotangent, energy_grad, energy_grad_host, energy_host,
+                  compile_excitations, energy, energy_cotangent, energy_grad, energy_grad_host, energy_grad_multi, energy_host,
                   kernel_launches, svd)
 
 __all__ = ["Circuit", "Hamiltonian", "State", "apply_circuit", "apply_circuit_host", "build_hamiltonian",
-           "compile_excitations", "energy", "energy_cotangent", "energy_grad", "energy_grad_host", "energy_host",
+           "compile_excitations", "energy", "energy_cotangent", "energy_grad", "energy_grad_host", "energy_grad_multi", "energy_host",
            "kernel_launches", "svd"]

@@ -74,6 +74,9 @@ _SIGS = {
                                   c_void_p, c_void_p]),
     "mps_energy_grad_dev": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p,
                                       c_void_p]),
+    "mps_set_svd_policy": (c_int32, [c_void_p, c_int32]),
+    "mps_energy_grad_multi": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                        c_void_p]),
     "mps_svd_dev": (c_int32, [c_int32, c_int32, c_void_p, c_int32, c_double, c_void_p, c_void_p, c_void_p,
                               c_void_p]),
     "mps_zgemm_mixed_dev": (c_int32, [c_int32, c_int32, c_int32, c_void_p, c_int32, c_int32, c_void_p, c_int32,

@@ -159,6 +159,11 @@ class State:
             o += e
         return dims, lams, B
 
+    def set_svd_policy(self, one_cta: bool) -> None:
+        """mps_set_svd_policy: True = one CTA per gate SVD always (for many concurrent problems),
+        False = automatic (the cooperative whole-GPU SVD for matrices above 128 on a side)."""
+        check(_lib.load().mps_set_svd_policy(self._h, 1 if one_cta else 0))
+
     def profile(self, enable: bool = True) -> None:
         """mps_profile: time every gate SVD with CUDA events and count its flops."""
         check(_lib.load().mps_profile(self._h, 1 if enable else 0))
@@ -300,6 +305,33 @@ def energy_grad(state0: State, circuit: Circuit, theta, ham: Hamiltonian, out=No
         return out
     E = float(E_out[0]) if ni == 1 else E_out
     return (E, g_out, gg) if gate_grad else (E, g_out)
+
+
+def energy_grad_multi(states, circuits, thetas, hams, outs=None):
+    """mps_energy_grad_multi: E and dE/dtheta of independent problems of uneven size, run
+    concurrently.  Problem i is energy_grad(states[i], circuits[i], thetas[i], hams[i]).
+
+    Returns (Es, grads): lists with each problem's E (float, or [n_inst] for a batched state) and
+    gradient.  `outs`: optional list of (E, grad) arrays/tensors receiving the results.
+    """
+    n = len(states)
+    if not (len(circuits) == len(thetas) == len(hams) == n) or n == 0:
+        raise ValueError("states, circuits, thetas and hams must be non-empty lists of one length")
+    thetas = [_f64(t) for t in thetas]
+    nth = [_n_theta(s, t) for s, t in zip(states, thetas)]
+    if outs is None:
+        outs = [(np.zeros(s.n_inst), np.zeros((s.n_inst, k) if s.n_inst > 1 else k)) for s, k in zip(states, nth)]
+    P = ctypes.c_void_p * n
+
+    def arr(ptrs):
+        return P(*[None if q is None else q.value for q in ptrs])
+
+    check(_lib.load().mps_energy_grad_multi(
+        n, arr([s._h for s in states]), arr([c._h for c in circuits]), arr([_ptr(t) for t in thetas]),
+        (ctypes.c_int32 * n)(*nth), arr([h._h for h in hams]), arr([_ptr(o[0]) for o in outs]),
+        arr([_ptr(o[1]) for o in outs])))
+    Es = [float(o[0][0]) if s.n_inst == 1 and isinstance(o[0], np.ndarray) else o[0] for s, o in zip(states, outs)]
+    return Es, [o[1] for o in outs]
 
 
 # ---- the host-argument calls of include/mps.h (gate list and Hamiltonian passed per call) -----

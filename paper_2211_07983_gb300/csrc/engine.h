@@ -90,6 +90,7 @@ struct Layout {
   std::vector<size_t> site_off;  // n+1 prefix offsets (complex elements)
   std::vector<size_t> lam_off;   // n+2 prefix offsets (doubles), slots 0..n
   int max_cap = 1;
+  bool one_cta_svd = false;      // policy: never the cooperative SVD (mps_set_svd_policy)
   void build(int n_, int D_);
   size_t site_cap(int s) const { return site_off[s + 1] - site_off[s]; }
   size_t site_elems() const { return site_off[n]; }

@@ -17,6 +17,9 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <string>
+#include <vector>
 #include <numeric>
 
 #include "engine.h"
@@ -227,13 +230,13 @@ struct Ctx {
   Batch bt;
 };
 
-// A gate on bond b runs the cooperative multi-SM SVD when the state holds one instance and the
-// gate's two-site matrix can exceed SVD_COOP_MIN_SIDE - 1 rows or columns.
+// A gate on bond b runs the cooperative multi-SM SVD when the state holds one instance, its
+// policy allows it, and the gate's two-site matrix can exceed SVD_COOP_MIN_SIDE - 1 rows or columns.
 static bool gate_uses_coop(const Layout& L, int n_inst, int b) {
-  return n_inst == 1 && std::max(2 * L.cap[b], 2 * L.cap[b + 2]) >= SVD_COOP_MIN_SIDE;
+  return !L.one_cta_svd && n_inst == 1 && std::max(2 * L.cap[b], 2 * L.cap[b + 2]) >= SVD_COOP_MIN_SIDE;
 }
 static bool state_uses_coop(const Layout& L, int n_inst) {
-  return n_inst == 1 && 2 * L.max_cap >= SVD_COOP_MIN_SIDE;
+  return !L.one_cta_svd && n_inst == 1 && 2 * L.max_cap >= SVD_COOP_MIN_SIDE;
 }
 
 static mps_status ensure_forward_scratch(const Layout& L, Workspace& w) {
@@ -1018,9 +1021,16 @@ static size_t stage_take(Workspace& w, size_t count) {
 
 // Ends a call: fetch the status word through the staging, wait for the stream, and copy the
 // host outputs out only when the call succeeded (outputs are untouched on error).
+static mps_status complete_call(mps_state* s, const char* where);
 static mps_status finish_call(mps_state* s, const char* where) {
   Workspace& w = *s->ws;
   launch_status_fetch(s->batch(), s->status.as<int>(), w.stage_dev, s->st);
+  return complete_call(s, where);
+}
+
+// The second half of finish_call, for calls whose status fetch is already enqueued.
+static mps_status complete_call(mps_state* s, const char* where) {
+  Workspace& w = *s->ws;
   if (!w.done) MPS_CU(cudaEventCreateWithFlags(&w.done, cudaEventBlockingSync | cudaEventDisableTiming));
   MPS_CU(cudaEventRecord(w.done, s->st));
   MPS_CU(cudaEventSynchronize(w.done));
@@ -1661,9 +1671,11 @@ namespace mpsi {
 // or tape and the gate matrices.
 enum RunMode { RUN_FULL = 0, RUN_BEGIN = 1, RUN_END = 2 };
 
+// With defer (RUN_FULL only) the call returns once everything, the status fetch included, is
+// enqueued on the state's stream; complete_call and harvest_profile finish it.
 static mps_status energy_grad_run(int mode, const mps_state* s0, const mps_circuit* c, const double* theta,
                                   int32_t n_theta, const mps_hamiltonian_dev* hc, double* E_out, double* grad_out,
-                                  double* gate_grad_out, double* Bbar_io) {
+                                  double* gate_grad_out, double* Bbar_io, bool defer = false) {
   const char* where = mode == RUN_FULL ? "mps_energy_grad" : mode == RUN_BEGIN ? "mps_energy_grad_shard_begin"
                                                                                : "mps_energy_grad_shard_end";
   if (!s0) return fail(MPS_EINVAL, std::string(where) + ": state is NULL");
@@ -1860,7 +1872,7 @@ static mps_status energy_grad_run(int mode, const mps_state* s0, const mps_circu
                                   w.gate_grad.p, w.grad.p, w.theta.p, w.G.p, w.dG.p, w.A.p, w.svd.p, w.C.p,
                                   w.Vs.p, w.s.p, w.stats.p, w.scalars.p, w.work.mem.p, w.rec.mem.p,
                                   ec, ec ? ec->bufs.p : nullptr, ec ? ec->tables.p : nullptr,
-                                  (const void*)(intptr_t)w.profile};
+                                  (const void*)(intptr_t)w.profile, (const void*)(intptr_t)L.one_cta_svd};
   for (auto& sp : w.snaps) key.push_back(sp->mem.p);
   if (w.graph_exec && key == w.graph_key) {
     MPS_CU(cudaGraphLaunch(w.graph_exec, s->st));
@@ -1901,8 +1913,39 @@ static mps_status energy_grad_run(int mode, const mps_state* s0, const mps_circu
   MPS_TRY(put_out(s, E_out, dE, 1));
   MPS_TRY(put_out(s, grad_out, w.grad.as<double>(), n_theta));
   MPS_TRY(put_out(s, gate_grad_out, w.gate_grad.as<double>(), ng));
+  if (defer) {
+    launch_status_fetch(s->batch(), s->status.as<int>(), w.stage_dev, s->st);
+    return MPS_OK;
+  }
   MPS_TRY(finish_call(s, "mps_energy_grad"));
   return harvest_profile(w);
+}
+
+// Streams and events of mps_energy_grad_multi, created once per device and kept.
+struct MultiPool {
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+};
+
+static mps_status multi_pool(int need, MultiPool** out) {
+  static std::mutex mu;
+  static std::map<int, MultiPool> pools;
+  int dev = 0;
+  MPS_CU(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  MultiPool& p = pools[dev];
+  while ((int)p.streams.size() < need) {
+    cudaStream_t st = nullptr;
+    MPS_CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    p.streams.push_back(st);
+  }
+  while ((int)p.events.size() < 2 * need) {
+    cudaEvent_t ev = nullptr;
+    MPS_CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    p.events.push_back(ev);
+  }
+  *out = &p;
+  return MPS_OK;
 }
 
 }  // namespace mpsi
@@ -1914,6 +1957,104 @@ mps_status mps_energy_grad_dev(const mps_state* s0, const mps_circuit* c, const 
                                double* gate_grad_out) {
   clear_error();
   return energy_grad_run(RUN_FULL, s0, c, theta, n_theta, hc, E_out, grad_out, gate_grad_out, nullptr);
+}
+
+mps_status mps_set_svd_policy(mps_state* s, int32_t policy) {
+  clear_error();
+  if (!s) return fail(MPS_EINVAL, "mps_set_svd_policy: state is NULL");
+  if (policy != MPS_SVD_AUTO && policy != MPS_SVD_ONE_CTA)
+    return fail(MPS_EINVAL, "mps_set_svd_policy: policy must be MPS_SVD_AUTO or MPS_SVD_ONE_CTA");
+  s->L.one_cta_svd = policy == MPS_SVD_ONE_CTA;
+  return MPS_OK;
+}
+
+mps_status mps_energy_grad_multi(int32_t n_prob, mps_state* const* states, const mps_circuit* const* circuits,
+                                 const double* const* theta, const int32_t* n_theta,
+                                 const mps_hamiltonian_dev* const* hams, double* const* E_out,
+                                 double* const* grad_out) {
+  clear_error();
+  if (n_prob < 1 || !states || !circuits || !theta || !n_theta || !hams || !E_out || !grad_out)
+    return fail(MPS_EINVAL, "mps_energy_grad_multi: NULL argument or n_prob < 1");
+  for (int i = 0; i < n_prob; ++i) {
+    if (!states[i] || !circuits[i] || !hams[i])
+      return fail(MPS_EINVAL, "mps_energy_grad_multi: NULL state, circuit or Hamiltonian at " + std::to_string(i));
+    for (int j = 0; j < i; ++j)
+      if (states[j] == states[i])
+        return fail(MPS_EINVAL, "mps_energy_grad_multi: the same state appears twice (" + std::to_string(j) +
+                                    ", " + std::to_string(i) + ")");
+  }
+  MultiPool* pool = nullptr;
+  MPS_TRY(multi_pool(n_prob + 1, &pool));
+  std::vector<cudaStream_t> saved_st(n_prob);
+  std::vector<void*> saved_cfg(n_prob);
+  std::vector<char> enqueued(n_prob, 0);
+  mps_status first = MPS_OK;
+  std::string first_msg;
+  auto note = [&](mps_status st) {
+    if (st != MPS_OK && first == MPS_OK) {
+      first = st;
+      first_msg = mps_last_error();
+    }
+  };
+  // every problem's own stream order: its pool stream starts after the work already on it
+  for (int i = 0; i < n_prob; ++i) {
+    mps_state* s = states[i];
+    saved_st[i] = s->st;
+    saved_cfg[i] = s->cfg.cuda_stream;
+    note(cudaEventRecord(pool->events[i], s->st) == cudaSuccess ? MPS_OK : fail(MPS_ECUDA, "event record"));
+  }
+  const cudaStream_t join = pool->streams[n_prob];
+  // problems on the one-CTA SVD: concurrently, one pool stream each
+  for (int i = 0; i < n_prob && first == MPS_OK; ++i) {
+    mps_state* s = states[i];
+    if (state_uses_coop(s->L, s->n_inst())) continue;
+    const cudaStream_t st = pool->streams[i];
+    if (cudaStreamWaitEvent(st, pool->events[i], 0) != cudaSuccess) {
+      note(fail(MPS_ECUDA, "stream wait"));
+      break;
+    }
+    s->st = st;
+    s->cfg.cuda_stream = st;
+    const mps_status r = energy_grad_run(RUN_FULL, s, circuits[i], theta[i], n_theta[i], hams[i], E_out[i],
+                                         grad_out[i], nullptr, nullptr, true);
+    note(r);
+    if (r == MPS_OK) {
+      enqueued[i] = 1;
+      note(cudaEventRecord(pool->events[n_prob + i], st) == cudaSuccess ? MPS_OK : fail(MPS_ECUDA, "event record"));
+      note(cudaStreamWaitEvent(join, pool->events[n_prob + i], 0) == cudaSuccess ? MPS_OK
+                                                                                  : fail(MPS_ECUDA, "stream wait"));
+    }
+  }
+  // problems on the cooperative (whole-GPU) SVD: one after another on the join stream, after all
+  // of the above, so that a cooperative grid never shares the GPU with them
+  for (int i = 0; i < n_prob && first == MPS_OK; ++i) {
+    mps_state* s = states[i];
+    if (!state_uses_coop(s->L, s->n_inst())) continue;
+    if (cudaStreamWaitEvent(join, pool->events[i], 0) != cudaSuccess) {
+      note(fail(MPS_ECUDA, "stream wait"));
+      break;
+    }
+    s->st = join;
+    s->cfg.cuda_stream = join;
+    note(energy_grad_run(RUN_FULL, s, circuits[i], theta[i], n_theta[i], hams[i], E_out[i], grad_out[i], nullptr,
+                         nullptr, false));
+  }
+  for (int i = 0; i < n_prob; ++i) {
+    if (enqueued[i]) {
+      mps_state* s = states[i];
+      note(complete_call(s, "mps_energy_grad_multi"));
+      note(harvest_profile(*s->ws));
+    }
+  }
+  if (first == MPS_OK && cudaStreamSynchronize(join) != cudaSuccess) note(fail(MPS_ECUDA, "join stream"));
+  if (first != MPS_OK)   // a problem that failed part-way may have left work on its pool stream
+    for (int i = 0; i <= n_prob; ++i) cudaStreamSynchronize(pool->streams[i]);
+  for (int i = 0; i < n_prob; ++i) {
+    states[i]->st = saved_st[i];
+    states[i]->cfg.cuda_stream = saved_cfg[i];
+  }
+  if (first != MPS_OK) return fail(first, first_msg);
+  return MPS_OK;
 }
 
 mps_status mps_energy_grad_shard_begin(const mps_state* s0, const mps_circuit* c, const double* theta,

@@ -155,6 +155,17 @@ def sd_excitations(n: int, n_e: int):
     return out
 
 
+def sampled_excitations(excs, n_single: int, n_double: int, seed: int):
+    """A seeded random choice of n_single singles and n_double doubles of `excs`, kept in list
+    order (singles first): the reduced circuit of a batch instance."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    singles = [e for e in excs if e[1] < 0]
+    doubles = [e for e in excs if e[1] >= 0]
+    ps = np.sort(rng.choice(len(singles), size=min(n_single, len(singles)), replace=False))
+    pd = np.sort(rng.choice(len(doubles), size=min(n_double, len(doubles)), replace=False))
+    return [singles[t] for t in ps] + [doubles[t] for t in pd]
+
+
 def mp2_like_scores(excs, hs, es):
     """Score |(ia|jb) - (ib|ja)| / max(|e_a + e_b - e_i - e_j|, 0.1), e_p = h_pp.
 
