@@ -305,6 +305,24 @@ mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, doub
                        double* V_out, double* W_out, int32_t* k_out);
 
 /*
+ * Autotuning of the one-CTA gate SVD's work split (no counterpart in the paper).  A column pair of
+ * a Jacobi round is handled by 8, 16 or 32 lanes, chosen separately for the FP32 and the FP64
+ * sweeps; without a tuned table a rule picks them from the number of pairs.
+ *   mps_svd_tune: mean device time in ms (*ms_out, from CUDA events on the default stream) of
+ *     `reps` (1..1000) SVDs of the row-major m x ncol complex matrix A (host or device; m, ncol
+ *     even, 2..128) by one CTA with jg32 / jg64 lanes per pair (8, 16, 32, or 0 for the rule),
+ *     after one warm-up.  Synchronises; MPS_ENOCONV etc. if the SVD fails.
+ *   mps_set_svd_tiles: installs the process-wide table used by every later one-CTA gate SVD whose
+ *     bond caps give an m_cap x n_cap matrix: n_entries rows of 4 ints {m_cap, n_cap, jg32, jg64}
+ *     (host; caps 2..512; lanes 0, 8, 16 or 32, 0 = the rule for that phase).  n_entries = 0
+ *     clears the table.  A captured evaluation graph keeps the choice it was captured with.
+ *     MPS_EINVAL for malformed entries (the table is then unchanged).
+ */
+mps_status mps_svd_tune(int32_t m, int32_t ncol, const double* A, int32_t jg32, int32_t jg64, int32_t reps,
+                        double* ms_out);
+mps_status mps_set_svd_tiles(int32_t n_entries, const int32_t* entries);
+
+/*
  * The gate SVD of mps_svd_dev without any memory allocation.  Some callers cannot call
  * cudaMalloc: embedders whose device memory is owned by another allocator (a framework's caching
  * allocator, a memory pool sized once at start-up) or that run under a fixed device-memory budget,

@@ -75,6 +75,8 @@ _SIGS = {
     "mps_energy_grad_dev": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p,
                                       c_void_p]),
     "mps_set_svd_policy": (c_int32, [c_void_p, c_int32]),
+    "mps_svd_tune": (c_int32, [c_int32, c_int32, c_void_p, c_int32, c_int32, c_int32, c_void_p]),
+    "mps_set_svd_tiles": (c_int32, [c_int32, c_void_p]),
     "mps_energy_grad_multi": (c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                         c_void_p]),
     "mps_svd_dev": (c_int32, [c_int32, c_int32, c_void_p, c_int32, c_double, c_void_p, c_void_p, c_void_p,

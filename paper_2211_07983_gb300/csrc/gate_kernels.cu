@@ -2,6 +2,9 @@
 // custom pieces of its exact adjoint (Sec. 4 / App. A rules), FP64.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "../../include/mps.h"
 #include "common.cuh"
@@ -115,7 +118,7 @@ __global__ void contract_kernel(const double2* __restrict__ Bl, const double2* _
 //
 // The two-site matrix C~ (m x n) is orthogonalised on its shorter side: for m >= n the n columns
 // of X0 = C~ are rotated (Q accumulates V), for m < n the m columns of X0 = C~^H (Q accumulates
-// U).  GB300 runs FP64 at 1/58 of its FP32 rate, so the sweeps first run in FP32 on a complex64
+// U).  GB300 runs FP64 at about 1/60 of its FP32 rate, so the sweeps first run in FP32 on a complex64
 // copy; the accumulated rotation is then re-orthonormalised in FP64 (modified Gram-Schmidt),
 // X = X0 Q is re-formed in FP64 from the untouched input, and FP64 sweeps (scaled rotations,
 // numerically-zero columns cleaned first) finish to the FP64 convergence criterion.  The result
@@ -155,8 +158,8 @@ struct Cplx<float> {
 
 // Cyclic (round-robin) sweeps over the K columns of X (R rows, column j at X + j*R) with the
 // rotations accumulated into Q (K x K, column j at Q + j*K).  A column pair is handled by a group
-// of 8 lanes, so one warp works on 4 pairs of a round at once: each lane strides over the rows by
-// 8, the inner product is reduced over the group in three shuffles, and the four pairs' memory
+// of JG lanes; with JG = 8 one warp works on 4 pairs of a round at once: each lane strides over
+// the rows by 8, the inner product is reduced over the group in three shuffles, and the pairs' memory
 // accesses and reductions overlap (instruction-level parallelism across pairs, which hides the
 // shared-memory and shuffle latencies that a warp-per-pair ordering exposes).  Column norms are
 // recomputed at the start of every sweep and updated by each rotation (alpha' = alpha - t g,
@@ -168,7 +171,7 @@ struct Cplx<float> {
 // in the working precision T, so every rotation is unitary to T's precision whatever the
 // accuracy of t (a t off by 1e-7 relative leaves |gamma| 1e-7 of its size, removed by the next
 // sweep at no extra sweep count, since the sweeps converge quadratically).  FP64 on GB300 runs at
-// 1/58 of the FP32 rate, and this keeps the divisions and square roots of a rotation in FP32.
+// about 1/60 of the FP32 rate, and this keeps the divisions and square roots of a rotation in FP32.
 //
 // Stopping: a sweep that rotates nothing.  This generic version runs the FP32 phase; the FP64
 // phase uses the scaled variant below, which also stops early.
@@ -545,14 +548,18 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(const SvdArgs p0, size
   __syncthreads();
   int conv = 0;
   const int npairs = (K + (K & 1)) / 2;   // column pairs per round
+  // lanes per column pair: the launcher's (tuned) choice, else enough lanes to use all 16 warps
+  // in the latency-bound FP32 phase, and 8 unless that would idle an FP64 pipe in the FP64 phase
+  const int g32 = p.jg32 > 0 ? p.jg32 : (npairs <= 16 ? 32 : npairs <= 32 ? 16 : 8);
+  const int g64 = p.jg64 > 0 ? p.jg64 : (npairs <= 4 ? 32 : npairs <= 8 ? 16 : 8);
   int sweeps32 = 0;
   {
     const float tol32 = 4.f * 1.1920929e-7f * sqrtf((float)R), tiny32 = (float)(1e-30 * fro2_sh) + 1e-37f;
     float* nrm32 = reinterpret_cast<float*>(s_sh);
     double* fl32 = p.stats ? p.stats + 1 : nullptr;
-    if (npairs <= 16)
+    if (g32 == 32)
       sweeps32 = jacobi_sweeps<float, 32>(X32, Q32, R, K, tol32, tiny32, 30, &flag_sh, &conv, nrm32, fl32);
-    else if (npairs <= 32)
+    else if (g32 == 16)
       sweeps32 = jacobi_sweeps<float, 16>(X32, Q32, R, K, tol32, tiny32, 30, &flag_sh, &conv, nrm32, fl32);
     else
       sweeps32 = jacobi_sweeps<float, 8>(X32, Q32, R, K, tol32, tiny32, 30, &flag_sh, &conv, nrm32, fl32);
@@ -646,10 +653,10 @@ __global__ void __launch_bounds__(SVD_THREADS) svd_kernel(const SvdArgs p0, size
   int sweeps64 = 0;
   {
     const double tiny64 = 1e-30 * fro2_sh, early64 = 100.0 * tol64 * tol64;
-    if (npairs <= 4)
+    if (g64 == 32)
       sweeps64 = jacobi_sweeps_scaled<32>(X64, Q64, R, K, tol64, tiny64, SVD_MAX_SWEEPS, &flag_sh, &notdone_sh,
                                           &conv_sh, s_sh, dsc_sh, esc_sh, &maxn_sh, p.stats, early64, 1e-5);
-    else if (npairs <= 8)
+    else if (g64 == 16)
       sweeps64 = jacobi_sweeps_scaled<16>(X64, Q64, R, K, tol64, tiny64, SVD_MAX_SWEEPS, &flag_sh, &notdone_sh,
                                           &conv_sh, s_sh, dsc_sh, esc_sh, &maxn_sh, p.stats, early64, 1e-5);
     else
@@ -1081,8 +1088,28 @@ static size_t svd_dynamic_limit() {
 
 bool svd_fits_smem(int m_cap, int n_cap) { return svd_smem_bytes(m_cap, n_cap) <= svd_dynamic_limit(); }
 
+namespace {
+std::mutex g_tiles_mu;
+std::map<std::pair<int, int>, std::pair<int, int>> g_tiles;
+}  // namespace
+
+void svd_tiles_set(const int* entries, int n) {
+  std::lock_guard<std::mutex> lock(g_tiles_mu);
+  g_tiles.clear();
+  for (int i = 0; i < n; ++i)
+    g_tiles[{entries[4 * i], entries[4 * i + 1]}] = {entries[4 * i + 2], entries[4 * i + 3]};
+}
+
+void svd_tiles_get(int m_cap, int n_cap, int* jg32, int* jg64) {
+  std::lock_guard<std::mutex> lock(g_tiles_mu);
+  const auto it = g_tiles.find({m_cap, n_cap});
+  *jg32 = it == g_tiles.end() ? 0 : it->second.first;
+  *jg64 = it == g_tiles.end() ? 0 : it->second.second;
+}
+
 void launch_svd(const Batch& bt, const SvdArgs& a, int m_cap, int n_cap, cudaStream_t st) {
   SvdArgs b = a;
+  if (b.jg32 == 0 && b.jg64 == 0) svd_tiles_get(m_cap, n_cap, &b.jg32, &b.jg64);
   size_t smem = 0;
   if (svd_fits_smem(m_cap, n_cap)) {
     b.scratch = nullptr;

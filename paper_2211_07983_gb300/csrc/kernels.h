@@ -91,11 +91,19 @@ struct SvdArgs {
   double* stats;   // optional, 10 doubles: [0] += FP64 flops, [1] += FP32 flops, [2] += kernel ns, [3] += 1,
                    // [4..7] += ns in FP32 sweeps / re-orthonormalisation and X0 Q / FP64 sweeps / output,
                    // [8], [9] += FP32 and FP64 sweeps run
+  int jg32, jg64;  // lanes per column pair of the FP32 / FP64 sweeps (8, 16 or 32); <= 0: a rule from
+                   // the pair count.  launch_svd replaces 0, 0 by the tuned table's entry
+                   // (svd_tiles_set) for the launch's caps, if it has one.
 };
 size_t svd_smem_bytes(int m_cap, int n_cap);
 bool svd_fits_smem(int m_cap, int n_cap);
 // one CTA per instance
 void launch_svd(const Batch& bt, const SvdArgs& a, int m_cap, int n_cap, cudaStream_t st);
+// The tuned table of lanes per column pair, keyed by the bond caps' matrix shape (m_cap, n_cap):
+// entries of 4 ints {m_cap, n_cap, jg32, jg64}; n = 0 clears it.  Read by launch_svd (a launch
+// captured in a graph keeps the choice it was captured with).
+void svd_tiles_set(const int* entries, int n);
+void svd_tiles_get(int m_cap, int n_cap, int* jg32, int* jg64);
 // The same SVD of one large matrix (one instance) over the whole GPU: a cooperative launch of one
 // CTA per SM with bounded grid barriers between Jacobi rounds (svd_coop.cu), FP64 sweeps.  scratch:
 // svd_coop_scratch_bytes(m_cap, n_cap) bytes of device memory; a.scratch is not used.

@@ -1160,6 +1160,70 @@ static mps_status check_circuit(const mps_state* s, const mps_circuit* c, int n_
   return MPS_OK;
 }
 
+// One matrix's SVD on the device, as the gate kernels see it: the row-major input A (host or
+// device, m x ncol complex) copied column-major, dims {m/2, 1, ncol/2}, lambda_left = 1.
+struct SvdJob {
+  DevBuf buf, status;
+  double2 *Acm = nullptr, *W = nullptr, *Vs = nullptr, *scratch = nullptr;
+  double *s = nullptr, *lam = nullptr, *one = nullptr;
+  int* dims = nullptr;
+  SvdArgs a{};
+};
+
+static mps_status svd_job_setup(SvdJob& j, int m, int ncol, const double* A, int D, double eps) {
+  const size_t mn = (size_t)m * ncol, Kc = (size_t)std::min(m, ncol);
+  const size_t sizes[] = {mn * 16, Kc * m * 16, Kc * ncol * 16, 2 * mn * 16 + Kc * Kc * 16, Kc * 8, Kc * 8, 256,
+                          (size_t)m * 8};
+  size_t bytes = 0;
+  for (size_t z : sizes) bytes += align256(z);
+  MPS_TRY(j.buf.alloc(bytes));
+  MPS_TRY(j.status.alloc(sizeof(int)));
+  MPS_CU(cudaMemset(j.status.p, 0, sizeof(int)));
+  char* p = j.buf.as<char>();
+  int part = 0;
+  auto take = [&]() {
+    char* q = p;
+    p += align256(sizes[part++]);
+    return q;
+  };
+  j.Acm = reinterpret_cast<double2*>(take());
+  j.W = reinterpret_cast<double2*>(take());
+  j.Vs = reinterpret_cast<double2*>(take());
+  j.scratch = reinterpret_cast<double2*>(take());
+  j.s = reinterpret_cast<double*>(take());
+  j.lam = reinterpret_cast<double*>(take());
+  j.dims = reinterpret_cast<int*>(take());
+  j.one = reinterpret_cast<double*>(take());
+  bool dev_in = false;
+  MPS_TRY(where_is(A, "mps_svd: A", &dev_in));
+  // row-major input -> column-major working copy (host transpose)
+  std::vector<double2> hin(mn), hcm(mn);
+  MPS_CU(cudaMemcpy(hin.data(), A, mn * 16, dev_in ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+  for (int r = 0; r < m; ++r)
+    for (int c = 0; c < ncol; ++c) hcm[(size_t)c * m + r] = hin[(size_t)r * ncol + c];
+  MPS_CU(cudaMemcpy(j.Acm, hcm.data(), mn * 16, cudaMemcpyHostToDevice));
+  int hd[3] = {m / 2, 1, ncol / 2};
+  MPS_CU(cudaMemcpy(j.dims, hd, sizeof(hd), cudaMemcpyHostToDevice));
+  std::vector<double> ones(m / 2, 1.0);
+  MPS_CU(cudaMemcpy(j.one, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice));
+  SvdArgs& a = j.a;
+  a.A = j.Acm;
+  a.scratch = j.scratch;
+  a.dims = j.dims;
+  a.b = 0;
+  a.D = D;
+  a.eps = eps;
+  a.Vs = j.Vs;
+  a.s = j.s;
+  a.lam_out = j.lam;
+  a.W = j.W;
+  a.tape_dims = nullptr;
+  a.lam_left = j.one;
+  a.lam_left_copy = nullptr;
+  a.status = j.status.as<int>();
+  return MPS_OK;
+}
+
 }  // namespace mpsi
 
 using namespace mpsi;
@@ -1529,62 +1593,19 @@ mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, doub
   if (m < 2 || ncol < 2 || (m & 1) || (ncol & 1) || m > 512 || ncol > 512)
     return fail(MPS_EINVAL, "mps_svd: m and ncol must be even and in 2..512");
   if (D < 1 || !(eps >= 0.0)) return fail(MPS_EINVAL, "mps_svd: bad D or eps");
-  const size_t mn = (size_t)m * ncol, Kc = (size_t)std::min(m, ncol);
-  DevBuf buf, status;
-  const size_t sizes[] = {mn * 16, mn * 16, Kc * m * 16, Kc * ncol * 16, 2 * mn * 16 + Kc * Kc * 16,
-                          Kc * 8, Kc * 8, 256, (size_t)m * 8};
-  size_t bytes = 0;
-  for (size_t z : sizes) bytes += align256(z);
-  MPS_TRY(buf.alloc(bytes));
-  MPS_TRY(status.alloc(sizeof(int)));
-  char* p = buf.as<char>();
-  int part = 0;
-  auto take = [&]() {
-    char* q = p;
-    p += align256(sizes[part++]);
-    return q;
-  };
-  double2* Ain = reinterpret_cast<double2*>(take());
-  double2* Acm = reinterpret_cast<double2*>(take());
-  double2* W = reinterpret_cast<double2*>(take());
-  double2* Vs = reinterpret_cast<double2*>(take());
-  double2* scratch = reinterpret_cast<double2*>(take());
-  double* s = reinterpret_cast<double*>(take());
-  double* lam = reinterpret_cast<double*>(take());
-  int* dims = reinterpret_cast<int*>(take());
-  double* one = reinterpret_cast<double*>(take());
-  bool dev_in = false;
-  MPS_TRY(where_is(A, "mps_svd: A", &dev_in));
   for (const void* o : {(const void*)s_out, (const void*)V_out, (const void*)W_out, (const void*)k_out}) {
     bool od = false;
     MPS_TRY(where_is(o, "mps_svd: an output array", &od));
   }
-  MPS_CU(cudaMemcpy(Ain, A, mn * 16, dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
-  int hd[3] = {m / 2, 1, ncol / 2};
-  MPS_CU(cudaMemcpy(dims, hd, sizeof(hd), cudaMemcpyHostToDevice));
-  std::vector<double> ones(m / 2, 1.0);
-  MPS_CU(cudaMemcpy(one, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice));
-  // row-major input -> column-major working copy (host transpose)
-  std::vector<double2> hin(mn), hcm(mn);
-  MPS_CU(cudaMemcpy(hin.data(), Ain, mn * 16, cudaMemcpyDeviceToHost));
-  for (int r = 0; r < m; ++r)
-    for (int c = 0; c < ncol; ++c) hcm[(size_t)c * m + r] = hin[(size_t)r * ncol + c];
-  MPS_CU(cudaMemcpy(Acm, hcm.data(), mn * 16, cudaMemcpyHostToDevice));
-  SvdArgs a{};
-  a.A = Acm;
-  a.scratch = scratch;
-  a.dims = dims;
-  a.b = 0;
-  a.D = D;
-  a.eps = eps;
-  a.Vs = Vs;
-  a.s = s;
-  a.lam_out = lam;
-  a.W = W;
-  a.tape_dims = nullptr;
-  a.lam_left = one;
-  a.lam_left_copy = nullptr;
-  a.status = status.as<int>();
+  const size_t Kc = (size_t)std::min(m, ncol);
+  SvdJob job;
+  MPS_TRY(svd_job_setup(job, m, ncol, A, D, eps));
+  SvdArgs& a = job.a;
+  DevBuf& status = job.status;
+  int* dims = job.dims;
+  double2* W = job.W;
+  double2* Vs = job.Vs;
+  double* s = job.s;
   DevBuf coop;
   if (std::max(m, ncol) >= SVD_COOP_MIN_SIDE) {   // the multi-SM SVD that large gates use
     MPS_TRY(coop.alloc(svd_coop_scratch_bytes(m, ncol)));
@@ -1616,6 +1637,57 @@ mps_status mps_svd_dev(int32_t m, int32_t ncol, const double* A, int32_t D, doub
   MPS_TRY(out(V_out, tV.data(), Kc * ncol * 16));
   MPS_TRY(out(W_out, tW.data(), Kc * m * 16));
   MPS_TRY(out(k_out, &k, sizeof(int)));
+  return MPS_OK;
+}
+
+mps_status mps_svd_tune(int32_t m, int32_t ncol, const double* A, int32_t jg32, int32_t jg64, int32_t reps,
+                        double* ms_out) {
+  clear_error();
+  if (!A || !ms_out) return fail(MPS_EINVAL, "mps_svd_tune: NULL argument");
+  if (m < 2 || ncol < 2 || (m & 1) || (ncol & 1) || std::max(m, ncol) >= SVD_COOP_MIN_SIDE)
+    return fail(MPS_EINVAL, "mps_svd_tune: m and ncol must be even and in 2..128");
+  auto ok_jg = [](int g) { return g == 0 || g == 8 || g == 16 || g == 32; };
+  if (!ok_jg(jg32) || !ok_jg(jg64)) return fail(MPS_EINVAL, "mps_svd_tune: lanes per pair must be 0, 8, 16 or 32");
+  if (reps < 1 || reps > 1000) return fail(MPS_EINVAL, "mps_svd_tune: reps must be in 1..1000");
+  SvdJob job;
+  MPS_TRY(svd_job_setup(job, m, ncol, A, std::min(m, ncol), 0.0));
+  // 0 asks for the kernel's rule; it is passed as -1 so that launch_svd does not read the table
+  job.a.jg32 = jg32 ? jg32 : -1;
+  job.a.jg64 = jg64 ? jg64 : -1;
+  const SvdArgs a = job.a;
+  auto launch = [&]() { launch_svd(Batch{1, 0}, a, m, ncol, 0); };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  MPS_CU(cudaEventCreate(&e0));
+  MPS_CU(cudaEventCreate(&e1));
+  launch();   // warm-up
+  MPS_CU(cudaEventRecord(e0, 0));
+  for (int r = 0; r < reps; ++r) launch();
+  MPS_CU(cudaEventRecord(e1, 0));
+  MPS_CU(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  const cudaError_t ce = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  MPS_CU(ce);
+  MPS_CU(cudaGetLastError());
+  int code = 0;
+  MPS_CU(cudaMemcpy(&code, job.status.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (code) return fail((mps_status)code, "mps_svd_tune: device status");
+  *ms_out = (double)ms / reps;
+  return MPS_OK;
+}
+
+mps_status mps_set_svd_tiles(int32_t n_entries, const int32_t* entries) {
+  clear_error();
+  if (n_entries < 0 || (n_entries > 0 && !entries)) return fail(MPS_EINVAL, "mps_set_svd_tiles: bad arguments");
+  for (int i = 0; i < n_entries; ++i) {
+    const int32_t* e = entries + 4 * i;
+    auto ok_jg = [](int g) { return g == 0 || g == 8 || g == 16 || g == 32; };
+    if (e[0] < 2 || e[1] < 2 || e[0] > 512 || e[1] > 512 || !ok_jg(e[2]) || !ok_jg(e[3]))
+      return fail(MPS_EINVAL, "mps_set_svd_tiles: entry " + std::to_string(i) +
+                                  " must be {m_cap, n_cap in 2..512, lanes 0/8/16/32, lanes 0/8/16/32}");
+  }
+  svd_tiles_set(entries, n_entries);
   return MPS_OK;
 }
 
