@@ -34,6 +34,33 @@ def test_table_save_load_and_validation(tmp_path):
     assert lib.mps_set_svd_tiles(0, None) == 0              # clears the table
 
 
+def test_tune_and_ensure_logic(tmp_path, monkeypatch):
+    """tune keeps a split only when it beats the rule by the margin; ensure tunes only the shapes
+    the saved table lacks, saves the union and installs it (timings and installation faked)."""
+    calls, installed = [], []
+
+    def fake_time(A, g32, g64, reps):
+        calls.append((A.shape, g32, g64))
+        if A.shape == (64, 64):
+            return {(0, 0): 1.0, (16, 8): 0.90}.get((g32, g64), 1.2)   # 10% better: kept
+        return {(0, 0): 1.0, (32, 32): 0.99}.get((g32, g64), 1.1)      # 1% better: rule kept
+    monkeypatch.setattr(autotune, "time_svd", fake_time)
+    monkeypatch.setattr(autotune, "apply", lambda rows: installed.append(list(rows)))
+    rows = autotune.tune([(64, 64), (8, 32)], reps=1)
+    assert [(r["jg32"], r["jg64"]) for r in rows] == [(16, 8), (0, 0)]
+    assert len(calls) == 2 * 10
+    path = str(tmp_path / "tiles.json")
+    calls.clear()
+    out = autotune.ensure([(64, 64)], path=path)
+    assert len(calls) == 10 and autotune.load(path) == out and installed[-1] == out
+    calls.clear()
+    out2 = autotune.ensure([(64, 64), (8, 32)], path=path)   # only the new shape is timed
+    assert {c[0] for c in calls} == {(8, 32)} and len(out2) == 2
+    calls.clear()
+    autotune.ensure([(8, 32)], path=path)                    # everything cached: nothing timed
+    assert calls == [] and installed[-1] == out2
+
+
 @pytest.mark.gpu
 def test_tuned_svd_variants_match_lapack():
     import torch
