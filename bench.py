@@ -581,15 +581,20 @@ def run_ours(args, rank, world, local):
         f64_l, f32_l = prof["fp64_flops"] / n_launch, prof["fp32_flops"] / n_launch
         p64, p32 = peaks["fp64_tflops"] * 1e12, peaks["fp32_tflops"] * 1e12
         achieved = (f64_l + f32_l * p64 / p32) / t_launch             # FP64-equivalent rate
+        # DRAM bytes (read + write) of one svd_kernel launch from an ncu capture of launch 3001 of
+        # `bench.py --profile-case step --workload n12_D64 --instances 4` (a 64-wide bond, 4 CTAs:
+        # 444,672 + 0 bytes), scaled to this launch's CTA count
+        traffic = 444672.0 / 4 * B
         roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": p64 / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / p64, "traffic": None,
+                "frac": achieved / p64, "traffic": traffic,
                 "kernel": f"svd_kernel (gate SVD; {B} CTAs per launch, one per instance)",
                 "per_launch": {"ms": 1e3 * t_launch, "fp64_flops": f64_l, "fp32_flops": f32_l,
                                "launches": n_launch},
                 "note": "achieved = (F64 + F32*P64/P32) flops per launch, counted on the device, / the launch's "
                         "CUDA-event duration on the state's stream over the timed steps; P64, P32 = FP64 and FP32 "
-                        "FMA peaks measured by libpeaks in this run (of measured); traffic null: the kernel works "
-                        "in shared memory (its DRAM bytes are in profiles/)",
+                        "FMA peaks measured by libpeaks in this run (of measured); traffic: dram__bytes_read.sum + "
+                        "dram__bytes_write.sum of one 4-CTA launch (a 64-wide bond) from one ncu capture, scaled to "
+                        "the launch's CTAs; the kernel works in shared memory, so this is the input matrix read once",
                 "svd_share_of_step": prof["svd_ms"] / 1e3 / (t_step * args.steps)}
     if rank == 0:
         cpu = None if args.no_cpu_baseline else (oracle_full(cfg) if n_exc is None else oracle_sample(cfg))
