@@ -743,6 +743,38 @@ def test_config2_doubles_against_oracle_values_and_32_central_differences(M):
     assert np.abs(fd[ok] - g[comps][ok]).max() <= 1e-7 * max(1.0, np.abs(g).max())
 
 
+@pytest.mark.parametrize("case", ["config2_doubles", "config4_prefix"])
+def test_mixed_precision_on_the_large_workloads(M, case):
+    """The mixed path (3xTF32 Pauli sweeps, tcgen05 for bond sides >= 64, and recomputed two-site
+    tensors; FP64 SVD, adjoint and cotangents) on the n = 20, D = 128 subset with doubles and the
+    n = 40, D = 256 prefix, against the oracle's stored FP64 values: 1e-6 relative in E, 1e-5 in
+    |dE/dtheta|."""
+    import json
+    import os
+    if case == "config4_prefix":
+        gold = _config4_golden()
+        p = S.make_problem(4)
+        excs = [p.excitations[t] for t in gold["prefix"]]
+    else:
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config2_doubles.json")
+        if not os.path.exists(path):
+            pytest.skip("tests/golden/config2_doubles.json not generated")
+        with open(path) as f:
+            gold = json.load(f)
+        p = S.make_problem(2)
+        excs = [p.excitations[t] for t in gold["subset"]]
+    th = np.array(gold["theta"])
+    x, z, c = M.build_hamiltonian(p.h, p.eri)
+    circ = M.Circuit(p.n, M.compile_excitations(p.n, excs))
+    ham = M.Hamiltonian(p.n, x, z, c)
+    st = M.State.product(p.bits, p.spec.D, p.spec.eps, checkpoint_every=512, precision="mixed")
+    E, g = M.energy_grad(st, circ, th, ham)
+    g_ref = np.array(gold["grad"])
+    assert abs(E - gold["E"]) <= MIXED_E_TOL * max(1.0, abs(gold["E"]))
+    assert np.linalg.norm(g - g_ref) <= MIXED_G_TOL * max(1.0, np.linalg.norm(g_ref))
+    assert E != gold["E"]   # the tensor-core sweeps ran
+
+
 def test_string_sharded_energy_grad_matches_the_whole_evaluation(M):
     """mps_energy_grad_shard_begin / _end on one GPU with the strings split three ways: the
     three ranks' (E_r, Bbar_r) summed (as the allreduce would) and one reverse pass give the
